@@ -1,0 +1,380 @@
+"""FP64 CPU oracle for the multilevel NMF of Gillis & Glineur,
+"A Multilevel Approach for Nonnegative Matrix Factorization" (arXiv:1009.0881).
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously correct
+statement of what the GPU library computes.  Only the test suite, the smoke check
+in ``__graft_entry__`` and the CPU-baseline leg of ``bench.py`` may import it.
+The CUDA library never calls it, shares no code with it and must fail loudly
+when its extension is missing instead of falling back here.
+
+Conventions (paper notation): M is m x n (column j = vectorised image j, pixel
+(y, x) of an H x W grid at row y*W + x), V is m x r, W is r x n.  Everything is
+float64.  Matrix products are numpy library calls; no step is blocked, fused or
+reordered beyond what the paper states.
+
+Readings of points the paper leaves open (each marked READING below):
+  * grid sides that are not 2^a + 1: coarse side = ceil(side / 2), coarse (i, j)
+    sits on fine (2i, 2j); border stencil weights are the in-bounds subset,
+    renormalised to sum 1 (this reproduces the printed 3x3 -> 2x2 example);
+  * prolongation at an even-size border averages over the in-bounds coarse
+    neighbours only;
+  * HALS with B_kk = 0 (resp. D_kk = 0) leaves that column of V (row of W)
+    unchanged;
+  * MU denominators are floored at EPS_MU = 1e-30;
+  * the time budget T of the cycles becomes a sweep budget K: a level gets
+    floor(K/4) pre-sweeps and floor(K/2) post-sweeps, the coarsest K sweeps
+    (Table 1: 3k, ..., 3k, 4k sweeps with K = 4k);
+  * NNLS (Appendix A.2) is Lawson-Hanson started from x = 0, with dual
+    tolerance 1e-12 * max(1, max |b|) and an outer-iteration cap of 3r.
+
+Pins: every function here is checked in tests/test_oracle_*.py against the
+printed operator examples of Section 4.2, closed forms, invariants (row sums,
+nonnegativity, monotone objective), brute-force minimisation on tiny inputs and
+the transfer-error bound of Section 4.1.  The paper's dataset tables (Tables
+3-5) cannot be reproduced without the datasets: parity unpinned for those
+numbers, which the oracle does not claim to match.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+EPS_MU = 1e-30
+
+
+# ---------------------------------------------------------------------------
+# Section 4.2: coarse grids
+# ---------------------------------------------------------------------------
+
+def coarse_grid(h: int, w: int) -> tuple[int, int]:
+    """Keep one point out of two in each direction (Section 4.2, Figure 2).
+
+    For a side 2^a + 1 this gives 2^(a-1) + 1.  READING for other sides:
+    ceil(side / 2), i.e. the points 0, 2, 4, ... of the finer grid.
+    """
+    return (h + 1) // 2, (w + 1) // 2
+
+
+def grid_hierarchy(h: int, w: int, levels: int) -> list[tuple[int, int]]:
+    """Grids of levels 1 (finest, the input) .. L (coarsest)."""
+    grids = [(h, w)]
+    for _ in range(levels - 1):
+        grids.append(coarse_grid(*grids[-1]))
+    return grids
+
+
+# ---------------------------------------------------------------------------
+# Section 4.2, Eq. (4.1): full-weighting restriction
+# ---------------------------------------------------------------------------
+
+def restriction_weight(dy: int, dx: int) -> float:
+    """Eq. (4.1): weight 4 at the centre, 2 on the edges, 1 at the corners (/16)."""
+    return float((2 - abs(dy)) * (2 - abs(dx)))
+
+
+def restrict(X: np.ndarray, h: int, w: int) -> np.ndarray:
+    """Column-wise restriction R X of an (h*w) x c matrix (Section 4.1, Eq. (4.1)).
+
+    Coarse pixel (i, j) is the weighted mean of the fine pixels (2i+dy, 2j+dx),
+    dy, dx in {-1, 0, 1}.  On the border only in-bounds fine pixels are kept and
+    the weights are divided by their sum ("weights adapted correspondingly").
+    """
+    X = np.asarray(X, dtype=np.float64)
+    assert X.shape[0] == h * w
+    hc, wc = coarse_grid(h, w)
+    out = np.zeros((hc * wc,) + X.shape[1:])
+    for i in range(hc):
+        for j in range(wc):
+            acc = np.zeros(X.shape[1:])
+            total = 0.0
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    y, x = 2 * i + dy, 2 * j + dx
+                    if 0 <= y < h and 0 <= x < w:
+                        wt = restriction_weight(dy, dx)
+                        acc = acc + wt * X[y * w + x]
+                        total += wt
+            out[i * wc + j] = acc / total
+    return out
+
+
+def restriction_matrix(h: int, w: int) -> np.ndarray:
+    """The matrix R in R_+^{m' x m} of the restriction (Section 4.1)."""
+    return restrict(np.eye(h * w), h, w)
+
+
+# ---------------------------------------------------------------------------
+# Section 4.2, Eq. (4.2): prolongation by the mean of coarse neighbours
+# ---------------------------------------------------------------------------
+
+def rd_half(k: int) -> tuple[int, ...]:
+    """rd(k/2) of Eq. (4.2): {k/2} for even k, {(k-1)/2, (k+1)/2} for odd k."""
+    if k % 2 == 0:
+        return (k // 2,)
+    return ((k - 1) // 2, (k + 1) // 2)
+
+
+def prolong(Y: np.ndarray, hc: int, wc: int, h: int, w: int) -> np.ndarray:
+    """Column-wise prolongation P Y of an (hc*wc) x c matrix to the h x w grid (Eq. (4.2)).
+
+    Fine pixel (i, j) is the mean of the coarse pixels (i', j') with
+    i' in rd(i/2), j' in rd(j/2).  READING: neighbours outside the coarse grid
+    (only possible at an even-size border) are dropped from the mean.
+    """
+    Y = np.asarray(Y, dtype=np.float64)
+    assert Y.shape[0] == hc * wc
+    out = np.zeros((h * w,) + Y.shape[1:])
+    for i in range(h):
+        for j in range(w):
+            nbrs = [(a, b) for a in rd_half(i) if a < hc for b in rd_half(j) if b < wc]
+            acc = np.zeros(Y.shape[1:])
+            for a, b in nbrs:
+                acc = acc + Y[a * wc + b]
+            out[i * w + j] = acc / len(nbrs)
+    return out
+
+
+def prolongation_matrix(hc: int, wc: int, h: int, w: int) -> np.ndarray:
+    """The matrix P in R_+^{m x m'} of the prolongation (Section 4.1)."""
+    return prolong(np.eye(hc * wc), hc, wc, h, w)
+
+
+def smoothness(M: np.ndarray, h: int, w: int) -> float:
+    """s_M = ||M - P(R(M))||_F / ||M||_F (Section 4.1)."""
+    hc, wc = coarse_grid(h, w)
+    PRM = prolong(restrict(M, h, w), hc, wc, h, w)
+    return float(np.linalg.norm(M - PRM) / np.linalg.norm(M))
+
+
+# ---------------------------------------------------------------------------
+# Objective, problem (NMF) of Section 2
+# ---------------------------------------------------------------------------
+
+def objective(M: np.ndarray, V: np.ndarray, W: np.ndarray) -> float:
+    """||M - VW||_F (the square root of the objective of problem (NMF))."""
+    E = np.asarray(M, np.float64) - np.asarray(V, np.float64) @ np.asarray(W, np.float64)
+    return float(np.sqrt(np.sum(E * E)))
+
+
+def objective_sq_expanded(M: np.ndarray, V: np.ndarray, W: np.ndarray) -> float:
+    """||M - VW||_F^2 by the column expansion of Eq. (6.1):
+    sum_j ||M_:j||^2 - 2 (M_:j^T V) W_:j + W_:j^T (V^T V) W_:j."""
+    total = 0.0
+    VtV = V.T @ V
+    for j in range(M.shape[1]):
+        mj = M[:, j]
+        wj = W[:, j]
+        total += mj @ mj - 2.0 * (mj @ V) @ wj + wj @ VtV @ wj
+    return float(total)
+
+
+# ---------------------------------------------------------------------------
+# Section 2.3, Algorithm HALS
+# ---------------------------------------------------------------------------
+
+def hals_update_V_column(V: np.ndarray, A: np.ndarray, B: np.ndarray, k: int) -> None:
+    """V_:k <- max(0, (A_:k - sum_{l != k} V_:l B_lk) / B_kk), in place.
+
+    READING: B_kk = 0 (row k of W is zero) leaves V_:k unchanged.
+    """
+    if B[k, k] <= 0.0:
+        return
+    others = [l for l in range(V.shape[1]) if l != k]
+    V[:, k] = np.maximum(0.0, (A[:, k] - V[:, others] @ B[others, k]) / B[k, k])
+
+
+def hals_update_W_row(W: np.ndarray, C: np.ndarray, D: np.ndarray, k: int) -> None:
+    """W_k: <- max(0, (C_k: - sum_{l != k} D_kl W_l:) / D_kk), in place.
+
+    READING: D_kk = 0 (column k of V is zero) leaves W_k: unchanged.
+    """
+    if D[k, k] <= 0.0:
+        return
+    others = [l for l in range(W.shape[0]) if l != k]
+    W[k, :] = np.maximum(0.0, (C[k, :] - D[k, others] @ W[others, :]) / D[k, k])
+
+
+def hals_sweep(M, V, W):
+    """One pass of the while-loop of Algorithm HALS: all columns of V, then all rows of W."""
+    V = np.array(V, dtype=np.float64)
+    W = np.array(W, dtype=np.float64)
+    A = M @ W.T
+    B = W @ W.T
+    for k in range(V.shape[1]):
+        hals_update_V_column(V, A, B, k)
+    C = V.T @ M
+    D = V.T @ V
+    for k in range(W.shape[0]):
+        hals_update_W_row(W, C, D, k)
+    return V, W
+
+
+# ---------------------------------------------------------------------------
+# Section 2.2, Algorithm MU (Lee and Seung)
+# ---------------------------------------------------------------------------
+
+def mu_sweep(M, V, W):
+    """V <- V o [M W^T] / [V (W W^T)], then W <- W o [V^T M] / [(V^T V) W] (new V).
+
+    READING: denominators are floored at EPS_MU (0/0 -> 0).
+    """
+    V = np.array(V, dtype=np.float64)
+    W = np.array(W, dtype=np.float64)
+    V = V * (M @ W.T) / np.maximum(V @ (W @ W.T), EPS_MU)
+    W = W * (V.T @ M) / np.maximum((V.T @ V) @ W, EPS_MU)
+    return V, W
+
+
+# ---------------------------------------------------------------------------
+# Section 2.1 / Appendix A.2: ANLS with active-set NNLS
+# ---------------------------------------------------------------------------
+
+class NNLSNotConverged(RuntimeError):
+    pass
+
+
+def nnls_active_set(G: np.ndarray, b: np.ndarray, max_outer: int | None = None) -> np.ndarray:
+    """argmin_{x >= 0} 1/2 x^T G x - b^T x, G = F^T F symmetric PSD.
+
+    Lawson-Hanson active-set method (Appendix A.2, steps 0-3): variables are
+    split into active (held at zero) and passive sets; the unconstrained least
+    squares problem on the passive set is solved through its normal equations
+    G_PP z_P = b_P; optimality is checked through the dual w = b - G x; an
+    infeasible passive solution is interpolated back towards the previous x,
+    so the objective decreases at every exchange.
+    """
+    G = np.asarray(G, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    r = b.shape[0]
+    if max_outer is None:
+        max_outer = 3 * r
+    tol = 1e-12 * max(1.0, float(np.max(np.abs(b))) if r else 1.0)
+    x = np.zeros(r)
+    passive = np.zeros(r, dtype=bool)
+    outer = 0
+    while True:
+        w = b - G @ x  # minus the gradient
+        candidates = (~passive) & (w > tol)
+        if not candidates.any():
+            return x
+        if outer >= max_outer:
+            raise NNLSNotConverged(f"no convergence after {outer} exchanges")
+        outer += 1
+        j = int(np.argmax(np.where(candidates, w, -np.inf)))
+        passive[j] = True
+        while True:
+            P = np.flatnonzero(passive)
+            z = np.zeros(r)
+            z[P] = np.linalg.solve(G[np.ix_(P, P)], b[P])
+            if np.all(z[P] > 0.0):
+                x = z
+                break
+            bad = P[z[P] <= 0.0]
+            ratios = x[bad] / (x[bad] - z[bad])
+            alpha = np.min(ratios)
+            x = x + alpha * (z - x)
+            x[bad[ratios <= alpha]] = 0.0  # the blocking variables land exactly on 0
+            passive = passive & (x > 0.0)
+            x[~passive] = 0.0
+
+
+def anls_sweep(M, V, W):
+    """One pass of Algorithm ANLS: V <- argmin_{V>=0} ||M-VW||, then W likewise.
+
+    The V-step splits into m NNLS problems in r variables sharing G = W W^T with
+    right-hand sides the rows of M W^T (Appendix A.2); the W-step into n problems
+    sharing V^T V with right-hand sides the columns of V^T M.  The incoming V is
+    not used (ANLS needs only W, Remark after Algorithm NI).
+    """
+    W = np.array(W, dtype=np.float64)
+    m = M.shape[0]
+    n = M.shape[1]
+    G = W @ W.T
+    A = M @ W.T
+    V = np.stack([nnls_active_set(G, A[i]) for i in range(m)])
+    D = V.T @ V
+    C = V.T @ M
+    W = np.stack([nnls_active_set(D, C[:, j]) for j in range(n)], axis=1)
+    return V, W
+
+
+SWEEPS = {"hals": hals_sweep, "mu": mu_sweep, "anls": anls_sweep}
+
+
+def smooth(M, V, W, algo: str, sweeps: int, trace=None, level: int = 1):
+    """Run ``sweeps`` iterations of the chosen NMF algorithm ("NMF algorithm(M, V, W, T)")."""
+    step = SWEEPS[algo]
+    for _ in range(sweeps):
+        V, W = step(M, V, W)
+        if trace is not None:
+            trace.append((level, objective(M, V, W)))
+    return V, W
+
+
+# ---------------------------------------------------------------------------
+# Section 4.3: multigrid cycles
+# ---------------------------------------------------------------------------
+
+def restrict_hierarchy(M: np.ndarray, h: int, w: int, levels: int) -> list[np.ndarray]:
+    """M at levels 1..L, each restricted once (footnote of Algorithm FMG)."""
+    Ms = [np.asarray(M, dtype=np.float64)]
+    grids = grid_hierarchy(h, w, levels)
+    for l in range(levels - 1):
+        Ms.append(restrict(Ms[-1], *grids[l]))
+    return Ms
+
+
+def vcycle(Ms, grids, V, W, algo: str, L: int, K: int, level: int = 0, hooks=None, trace=None):
+    """Algorithm V-cycle with the sweep reading of Table 1.
+
+    L = 1: K sweeps.  Otherwise: floor(K/4) sweeps; restrict V; V-cycle on the
+    next coarser level with the same K (a quarter of the time at a level four
+    times cheaper); prolong V; floor(K/2) sweeps.  W is never transferred.
+    """
+    M = Ms[level]
+    if L == 1:
+        return smooth(M, V, W, algo, K, trace, level + 1)
+    V, W = smooth(M, V, W, algo, K // 4, trace, level + 1)
+    Vc = restrict(V, *grids[level])
+    Vc, W = vcycle(Ms, grids, Vc, W, algo, L - 1, K, level + 1, hooks, trace)
+    V = prolong(Vc, *grids[level + 1], *grids[level])
+    if hooks is not None:
+        hooks.append(("prolong", level, Vc.copy(), V.copy(), W.copy()))
+    return smooth(M, V, W, algo, K // 2, trace, level + 1)
+
+
+def nested_iteration(Ms, grids, V0, W0, algo: str, L: int, K: int, level: int = 0, trace=None):
+    """Algorithm NI: solve on the coarser level (K coarse sweeps), prolong, then floor(3K/4) sweeps."""
+    M = Ms[level]
+    if L == 1:
+        return smooth(M, V0, W0, algo, K, trace, level + 1)
+    Vc0 = restrict(V0, *grids[level])
+    Vc, W = nested_iteration(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace)
+    V = prolong(Vc, *grids[level + 1], *grids[level])
+    return smooth(M, V, W, algo, (3 * K) // 4, trace, level + 1)
+
+
+def full_multigrid(Ms, grids, V0, W0, algo: str, L: int, K: int, level: int = 0, trace=None):
+    """Algorithm FMG: FMG on the coarser level (budget K), prolong, then a V-cycle with budget floor(3K/4)."""
+    M = Ms[level]
+    if L == 1:
+        return smooth(M, V0, W0, algo, K, trace, level + 1)
+    Vc0 = restrict(V0, *grids[level])
+    Vc, W = full_multigrid(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace)
+    V = prolong(Vc, *grids[level + 1], *grids[level])
+    return vcycle(Ms, grids, V, W, algo, L, (3 * K) // 4, level, None, trace)
+
+
+CYCLES = {"vcycle": vcycle, "ni": nested_iteration, "fmg": full_multigrid}
+
+
+def solve(M, grid_h: int, grid_w: int, V0, W0, algo: str = "hals", levels: int = 1, K: int = 100,
+          cycle: str = "vcycle", trace=None):
+    """Multilevel NMF of M (m = grid_h * grid_w rows) from (V0, W0); returns (V, W)."""
+    M = np.asarray(M, dtype=np.float64)
+    Ms = restrict_hierarchy(M, grid_h, grid_w, levels)
+    grids = grid_hierarchy(grid_h, grid_w, levels)
+    V = np.asarray(V0, dtype=np.float64)
+    W = np.asarray(W0, dtype=np.float64)
+    if cycle == "vcycle":
+        return vcycle(Ms, grids, V, W, algo, levels, K, trace=trace)
+    return CYCLES[cycle](Ms, grids, V, W, algo, levels, K, trace=trace)

@@ -1,0 +1,114 @@
+"""Pins for the oracle's multigrid cycles (Section 4.3, Table 1, Section 4.1 bound)."""
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import nmf_oracle as o
+from paper_1009_0881_gb300 import synth
+
+
+def _table1_rows():
+    rows = []
+    with open(f"{ROOT}/tests/golden/sweep_allocation_table1.txt") as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(t) for t in line.split()])
+    return rows
+
+
+def _count_sweeps(cycle, L, K, h=16, w=16):
+    """Sweeps per level of a cycle, counted by replacing the inner algorithm with a counter."""
+    counts = [0] * L
+    p = synth.make_problem(h, w, 4, 2, data_seed=1)
+    trace = []
+    orig = dict(o.SWEEPS)
+    o.SWEEPS["count"] = lambda M, V, W: (V, W)
+    try:
+        o.solve(p.M, h, w, p.V, p.W, algo="count", levels=L, K=K, cycle=cycle, trace=trace)
+    finally:
+        o.SWEEPS.clear()
+        o.SWEEPS.update(orig)
+    for level, _ in trace:
+        counts[level - 1] += 1
+    return counts
+
+
+@pytest.mark.parametrize("row", _table1_rows())
+def test_vcycle_sweep_allocation_matches_table1(row):
+    L, k = row[0], row[1]
+    assert _count_sweeps("vcycle", L, 4 * k) == row[2:]
+
+
+@pytest.mark.parametrize("row", _table1_rows())
+def test_nested_iteration_sweep_allocation_matches_table1(row):
+    L, k = row[0], row[1]
+    assert _count_sweeps("ni", L, 4 * k) == row[2:]
+
+
+def test_fmg_allocation():
+    # FMG(L, K) = FMG(L-1, K) on the coarser level, then V-cycle(L, 3K/4)
+    K = 400
+    assert _count_sweeps("fmg", 1, K) == [K]
+    # L = 2: coarse gets K (the recursive FMG) + 3K/4 (inside the V-cycle); fine gets 3/4 * 3K/4
+    Kv = 3 * K // 4
+    assert _count_sweeps("fmg", 2, K) == [Kv // 4 + Kv // 2, K + Kv]
+
+
+def test_single_level_cycles_equal_plain_algorithm():
+    p = synth.make_problem(8, 8, 20, 3, data_seed=2)
+    M = p.M.astype(np.float64)
+    Vp, Wp = o.smooth(M, p.V.astype(np.float64), p.W.astype(np.float64), "hals", 7)
+    for cyc in ("vcycle", "ni", "fmg"):
+        V, W = o.solve(p.M, 8, 8, p.V, p.W, "hals", levels=1, K=7, cycle=cyc)
+        np.testing.assert_array_equal(V, Vp)
+        np.testing.assert_array_equal(W, Wp)
+
+
+def test_w_passes_through_transfers_unchanged():
+    # Only V is restricted and prolonged; W leaves the coarse level as it entered the prolongation
+    p = synth.make_problem(9, 9, 30, 4, data_seed=3)
+    hooks = []
+    Ms = o.restrict_hierarchy(p.M, 9, 9, 2)
+    grids = o.grid_hierarchy(9, 9, 2)
+    o.vcycle(Ms, grids, p.V.astype(np.float64), p.W.astype(np.float64), "hals", 2, 8, hooks=hooks)
+    (_, level, Vc, V, W), = hooks
+    np.testing.assert_allclose(V, o.prolong(Vc, *grids[1], *grids[0]))
+
+
+@pytest.mark.parametrize("algo", ["hals", "mu"])
+def test_transfer_error_bound_at_every_prolongation(algo):
+    # Section 4.1: ||M - P(V')W|| <= s_M ||M|| + ||P||_F ||R(M) - V'W||
+    p = synth.make_problem(19, 19, 60, 6, data_seed=4)
+    Ms = o.restrict_hierarchy(p.M, 19, 19, 3)
+    grids = o.grid_hierarchy(19, 19, 3)
+    hooks = []
+    o.vcycle(Ms, grids, p.V.astype(np.float64), p.W.astype(np.float64), algo, 3, 8, hooks=hooks)
+    assert len(hooks) == 2
+    for _, level, Vc, V, W in hooks:
+        M = Ms[level]
+        h, w = grids[level]
+        hc, wc = grids[level + 1]
+        P = o.prolongation_matrix(hc, wc, h, w)
+        lhs = np.linalg.norm(M - V @ W)
+        sM = o.smoothness(M, h, w)
+        rhs = sM * np.linalg.norm(M) + np.linalg.norm(P) * np.linalg.norm(Ms[level + 1] - Vc @ W)
+        assert lhs <= rhs * (1 + 1e-12)
+
+
+def test_multilevel_beats_single_level_on_smooth_data_mu():
+    # Sections 4.4 and 5.1 (qualitative): at equal fine-level-equivalent work, MU gains most
+    p = synth.make_problem(19, 19, 120, 8, data_seed=5)
+    M = p.M.astype(np.float64)
+    K = 40
+    V1, W1 = o.solve(p.M, 19, 19, p.V, p.W, "mu", levels=1, K=K)
+    V3, W3 = o.solve(p.M, 19, 19, p.V, p.W, "mu", levels=3, K=K)
+    assert o.objective(M, V3, W3) < o.objective(M, V1, W1)
+
+
+def test_anls_vcycle_independent_of_v_transfers():
+    # Remark after Algorithm NI: ANLS only needs W, so V's transfers do not change its result
+    p = synth.make_problem(8, 8, 15, 3, data_seed=6)
+    Va, Wa = o.solve(p.M, 8, 8, p.V, p.W, "anls", levels=2, K=8)
+    Vb, Wb = o.solve(p.M, 8, 8, np.zeros_like(p.V), p.W, "anls", levels=2, K=8)
+    np.testing.assert_array_equal(Va, Vb)
+    np.testing.assert_array_equal(Wa, Wb)
