@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Benchmark of the multilevel NMF hot path on GB300.
+
+One step = one complete multilevel solve through the C ABI: restriction of M
+to every level, the V-cycle schedule of HALS sweeps (pre-smoothing,
+restriction of V, coarse cycle, prolongation, post-smoothing) and the final
+||M - VW||_F, on the 19 x 19-grid workload (m = 361 pixels, n = 2429 images,
+r = 49; the CBCL face-database shape) with L = 3 levels and sweep budget
+K = 500 (1250 sweeps over the three levels).  Inputs are synthetic (seeded
+generator, paper_1009_0881_gb300/synth.py).
+
+  value  sweeps per second (all levels) with inputs resident in HBM
+  e2e    the same through nmf_solve on pinned host buffers (H2D + D2H timed)
+
+Also reported: time to reach (1 + 1e-3) times the FP64 oracle's final
+objective, the plain single-level FP32 path, a roofline of the dominant
+kernel (CUDA events per launch, live), the CPU oracle's speed, SM clocks.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-3 rel objective & sweeps/s vs plain FP32; served p50/p99 latency"
+WORKLOAD = "grid19_n2429_r49"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--algo", default="hals")
+    ap.add_argument("--levels", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--_oracle_sample", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm): run in a single-threaded child
+# ---------------------------------------------------------------------------
+def oracle_sample_child(args):
+    import numpy as np  # noqa: F401
+
+    from oracle import nmf_oracle as o
+    from paper_1009_0881_gb300 import synth
+
+    gh, gw, n, r, sigma = synth.WORKLOADS[args.workload]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    sweeps = sum(_schedule_py(args.levels, args.iters))
+    t0 = time.perf_counter()
+    o.solve(p.M, gh, gw, p.V, p.W, args.algo, levels=args.levels, K=args.iters)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"sweeps": sweeps, "seconds": dt}))
+
+
+def _schedule_py(L, K):
+    counts = [0] * L
+    for lvl in range(L - 1):
+        counts[lvl] = K // 4 + K // 2
+    counts[L - 1] = K
+    return counts
+
+
+def run_oracle_sample(args, K=None, levels=None):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle_sample", "--workload", args.workload, "--algo",
+           args.algo, "--levels", str(levels or args.levels), "--iters", str(K or args.iters)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True).stdout.strip().splitlines()[-1]
+    return json.loads(out)
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    samples = []
+    for _ in range(args.warmup):
+        run_oracle_sample(args, K=40)
+    for _ in range(args.steps):
+        samples.append(run_oracle_sample(args, K=40))
+    sweeps = sum(s["sweeps"] for s in samples)
+    secs = sum(s["seconds"] for s in samples)
+    value = sweeps / secs
+    desc = (f"FP64 numpy oracle, single thread, {args.workload} {args.algo} V-cycle L={args.levels} with K=40 "
+            f"({samples[0]['sweeps']} sweeps) per step instead of K={args.iters}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "algo": args.algo, "levels": args.levels, "iters": 40},
+        "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in rows:
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax = float(row[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if v.strip().lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1009_0881_gb300 import native, synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # CPU baseline before any GPU work (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = run_oracle_sample(args)
+        cpu = {"value": s["sweeps"] / s["seconds"], "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+               "sample": (f"the whole step once: FP64 numpy oracle, one thread, {args.workload} {args.algo} "
+                          f"V-cycle L={args.levels} K={args.iters} ({s['sweeps']} sweeps in {s['seconds']:.1f} s)")}
+
+    from paper_1009_0881_gb300 import build
+    build.build()
+    gh, gw, n, r, sigma = synth.WORKLOADS[args.workload]
+    # independent problem per rank (replicas): weak scaling
+    prob = synth.make_problem(gh, gw, n, r, sigma=sigma, data_seed=1 + rank)
+    m = gh * gw
+    sched = native.schedule("vcycle", args.levels, args.iters)
+    sweeps_per_step = sum(sched)
+
+    h = native.Handle(local)
+    stream = torch.cuda.current_stream(dev)
+    h.set_stream(stream.cuda_stream)
+    Md = torch.from_numpy(prob.M).to(dev)
+    V0d = torch.from_numpy(prob.V).to(dev)
+    W0d = torch.from_numpy(prob.W).to(dev)
+    Vd = torch.empty_like(V0d)
+    Wd = torch.empty_like(W0d)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    err = {}
+
+    def step():
+        Vd.copy_(V0d)
+        Wd.copy_(W0d)
+        h.solve(Md, gh, gw, Vd, Wd, args.algo, levels=args.levels, iters=args.iters)
+        err["f"] = h.error(Md, Vd, Wd)
+
+    launches_per_step = 0
+    for _ in range(args.warmup):
+        step()
+    step()
+    launches_per_step = h.last_launch_count()  # error call
+    Vd.copy_(V0d)
+    Wd.copy_(W0d)
+    h.solve(Md, gh, gw, Vd, Wd, args.algo, levels=args.levels, iters=args.iters)
+    launches_per_step += h.last_launch_count()
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = sum(times)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * sweeps_per_step * args.steps / (total_ms / 1e3)
+
+    # --- e2e through nmf_solve on pinned host buffers -----------------------
+    Mh = torch.from_numpy(prob.M).pin_memory()
+    Vh = torch.empty(prob.V.shape, dtype=torch.float32).pin_memory()
+    Wh = torch.empty(prob.W.shape, dtype=torch.float32).pin_memory()
+    V0h = torch.from_numpy(prob.V)
+    W0h = torch.from_numpy(prob.W)
+
+    def e2e_step():
+        Vh.copy_(V0h)
+        Wh.copy_(W0h)
+        h.solve(Mh, gh, gw, Vh, Wh, args.algo, levels=args.levels, iters=args.iters)
+        err["fh"] = h.error(Mh, Vh, Wh)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = sum(e2e_times) / args.steps
+    h2d = 2 * (prob.M.nbytes + prob.V.nbytes + prob.W.nbytes)  # solve + error each stage M, V, W
+    d2h = prob.V.nbytes + prob.W.nbytes + 8
+
+    extra = {}
+    if rank == 0:
+        extra = analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m, n, r)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator, CBCL-shaped 19x19 images)",
+            "config": {"workload": f"{args.workload}: 19x19 grid, m={m}, n={n}, r={r}; {args.algo} V-cycle "
+                                   f"L={args.levels} K={args.iters} ({sweeps_per_step} sweeps) + final error",
+                       "algo": args.algo, "levels": args.levels, "iters": args.iters,
+                       "sweeps_per_step": sweeps_per_step, "sweeps_per_level": sched,
+                       "l2": "inputs (3.5 MB) fit in L2: a 258 MB buffer is written between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": world * sweeps_per_step / (e2e_ms / 1e3), "unit": "sweeps/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+        line.update(extra)
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m, n, r):
+    """Time-to-target, the plain single-level path, and the roofline of the dominant kernel."""
+    import numpy as np
+    import torch
+
+    from paper_1009_0881_gb300 import native
+
+    out = {}
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "objectives.json")))
+    key = f"grid19_{args.algo}_L{args.levels}_K{args.iters}"
+    fstar = golden.get(key, {}).get("objective") if args.workload == WORKLOAD else None
+    out["objective"] = {"gpu": err["f"], "oracle_fp64": fstar,
+                        "rel_diff": None if fstar is None else abs(err["f"] - fstar) / fstar}
+    if fstar is not None:
+        target = (1 + 1e-3) * fstar
+        Vd.copy_(V0d)
+        Wd.copy_(W0d)
+        cap = sched[0]
+        tr = h.solve(Md, gh, gw, Vd, Wd, args.algo, levels=args.levels, iters=args.iters, trace_len=cap)
+        hit = np.nonzero(tr <= target)[0]
+        ttt = None
+        if len(hit):
+            # schedule position of that fine-level sweep: all coarse sweeps precede the post-smoothing
+            s_fine = int(hit[0]) + 1
+            pre = args.iters // 4
+            stop = s_fine if s_fine <= pre else s_fine + sum(sched[1:])
+            ms = []
+            for _ in range(args.warmup + args.steps):
+                Vd.copy_(V0d)
+                Wd.copy_(W0d)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.solve(Md, gh, gw, Vd, Wd, args.algo, levels=args.levels, iters=args.iters, stop_after=stop)
+                f = h.error(Md, Vd, Wd)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            assert f <= target * (1 + 1e-12), (f, target)
+            ttt = {"ms": statistics.median(ms[args.warmup:]), "sweeps": stop, "fine_sweeps": s_fine}
+        out["time_to_target"] = {"target": "(1+1e-3) x FP64 oracle objective of the same cycle",
+                                 "objective_target": target, "multilevel": ttt}
+        # plain single-level FP32 path with the same sweep budget K
+        plain = {}
+        ms = []
+        for _ in range(2 + 3):
+            Vd.copy_(V0d)
+            Wd.copy_(W0d)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tr1 = h.solve(Md, gh, gw, Vd, Wd, args.algo, levels=1, iters=args.iters, trace_len=args.iters)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        plain["sweeps_per_s_with_trace"] = args.iters / (statistics.median(ms[2:]) / 1e3)
+        Vd.copy_(V0d)
+        Wd.copy_(W0d)
+        ms = []
+        for _ in range(2 + 3):
+            Vd.copy_(V0d)
+            Wd.copy_(W0d)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.solve(Md, gh, gw, Vd, Wd, args.algo, levels=1, iters=args.iters)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        plain["sweeps_per_s"] = args.iters / (statistics.median(ms[2:]) / 1e3)
+        plain["ms_per_solve"] = statistics.median(ms[2:])
+        plain["final_objective"] = float(tr1[-1])
+        hit1 = np.nonzero(tr1 <= target)[0]
+        plain["reaches_target_after_sweeps"] = int(hit1[0]) + 1 if len(hit1) else None
+        out["plain_fp32_single_level"] = plain
+
+    out["roofline"], out["kernel_times_per_step_ms"] = roofline(args, h, Md, gh, gw, n, r, sched)
+    return out
+
+
+def roofline(args, h, Md, gh, gw, n, r, sched):
+    """Per-kernel CUDA-event timing at each level's size, weighted by the sweep schedule.
+
+    Algorithmic flops per launch (Appendix A.1 accounting, multiply-add = 2):
+      V-step products  A = M W^T, B = W W^T : 2 m_l n r + 2 n r^2
+      W-step products  C = V^T M, D = V^T V : 2 m_l n r + 2 m_l r^2
+      V update 2 m_l r^2,  W update 2 n r^2  (the V(WW^T) / (V^T V)W products)
+    """
+    import torch
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sms, _ = h.device_info()
+    fp32_peak = n_sms * 128 * 2 * sm_mhz * 1e6  # FFMA lanes x 2 flops x clock
+    dev = Md.device
+    Ml = Md
+    hh, ww = gh, gw
+    kinds = {"products (gemm_tn_kernel)": [0.0, 0.0, 0], "update (rows_update_kernel)": [0.0, 0.0, 0],
+             "error (error_tile_kernel)": [0.0, 0.0, 0]}
+    g = torch.Generator(device="cpu").manual_seed(0)
+    W = torch.rand(r, n, generator=g).to(dev)
+    for lvl, count in enumerate(sched):
+        ml = hh * ww
+        V = torch.rand(ml, r, generator=g).to(dev)
+        t = h.profile_sweep(Ml, V, W, args.algo, reps=50)
+        fl = [2 * ml * n * r + 2 * n * r * r, 2 * ml * r * r, 2 * ml * n * r + 2 * ml * r * r, 2 * n * r * r,
+              2 * ml * n * r]
+        for ph, kind in ((0, "products (gemm_tn_kernel)"), (2, "products (gemm_tn_kernel)"),
+                         (1, "update (rows_update_kernel)"), (3, "update (rows_update_kernel)")):
+            kinds[kind][0] += count * t[ph]
+            kinds[kind][1] += count * fl[ph]
+            kinds[kind][2] += count
+        if lvl == 0:
+            kinds["error (error_tile_kernel)"] = [t[4], fl[4], 1]
+        if lvl + 1 < len(sched):
+            hc, wc = (hh + 1) // 2, (ww + 1) // 2
+            Mc = torch.empty(hc * wc, n, device=dev)
+            h.restrict(Ml, hh, ww, Mc)
+            Ml, hh, ww = Mc, hc, wc
+    times = {k: v[0] for k, v in kinds.items()}
+    dom = max(times, key=times.get)
+    ms, flops, launches = kinds[dom]
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = fp32_peak / 1e12
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "launches_per_step": launches,
+            "mean_launch_us": 1e3 * ms / launches,
+            "peak_basis": f"FP32 FFMA: {n_sms} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (derived)"}
+    return roof, times
+
+
+
+if __name__ == "__main__":
+    a = parse_args()
+    if a._oracle_sample:
+        oracle_sample_child(a)
+    elif a.impl == "reference":
+        reference_arm(a)
+    else:
+        main_ours(a)

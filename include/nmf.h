@@ -1,0 +1,198 @@
+/*
+ * nmf.h - C ABI of the GB300 multilevel nonnegative matrix factorisation library.
+ *
+ * Method: N. Gillis and F. Glineur, "A Multilevel Approach for Nonnegative
+ * Matrix Factorization" (arXiv:1009.0881).  Given M >= 0 (m x n, one image of
+ * an H x W pixel grid per column) and a rank r, the library computes V >= 0
+ * (m x r) and W >= 0 (r x n) with M ~ VW (problem (NMF), Section 2), running
+ * HALS (Algorithm HALS, Section 2.3), MU (Algorithm MU, Section 2.2) or ANLS
+ * (Algorithm ANLS, Section 2.1 and Appendix A.2) sweeps inside the multigrid
+ * cycles of Section 4.3 (V-cycle, nested iteration, full multigrid) over a
+ * hierarchy of 2x2-coarsened pixel grids with the full-weighting restriction
+ * of Eq. (4.1) and the prolongation of Eq. (4.2).
+ *
+ * Common conventions
+ *  - All matrices are dense, row-major, float32, with no padding: M[i*n + j],
+ *    V[i*r + k], W[k*n + j].  Pixel (y, x) of the grid is row y*grid_w + x.
+ *  - A matrix pointer may address host memory (pageable or pinned) or device
+ *    memory of the handle's device; the library asks the driver which
+ *    (cudaPointerGetAttributes) and stages host data itself.  The caller owns
+ *    every pointer it passes; the library never frees or keeps caller memory.
+ *  - Every call runs on the handle's stream and has finished (results in
+ *    place, host or device) when it returns.  A handle is not thread-safe:
+ *    calls on one handle must not overlap.
+ *  - Return values: NMF_OK (0) or a negative nmf_status; nmf_last_error()
+ *    then returns a human-readable reason.  On error the output arrays are
+ *    unspecified unless stated otherwise.
+ *  - Limits: 1 <= r <= 64, m, n >= 1, 1 <= levels <= 16.
+ */
+#ifndef GB300_NMF_H
+#define GB300_NMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nmf_ctx* nmf_handle;
+
+/* Inner NMF algorithm ("smoother") run at every level. */
+typedef enum {
+    NMF_HALS = 0, /* Algorithm HALS (Section 2.3): r exact column updates of V, then r row updates of W */
+    NMF_MU = 1,   /* Algorithm MU (Section 2.2): Lee-Seung multiplicative updates */
+    NMF_ANLS = 2  /* Algorithm ANLS (Section 2.1, Appendix A.2): exact NNLS for V then W (FP64 active set) */
+} nmf_algo;
+
+/* Storage precision of M and of the GEMM operands. */
+typedef enum {
+    NMF_FP32 = 0, /* everything float32 */
+    NMF_BF16 = 1  /* M, V, W as bfloat16 GEMM operands, float32 accumulation and updates */
+} nmf_precision;
+
+/* Multigrid cycle (Section 4.3). */
+typedef enum {
+    NMF_VCYCLE = 0, /* Algorithm V-cycle (Section 4.3.2) */
+    NMF_NESTED = 1, /* Algorithm Nested Iteration (Section 4.3.1) */
+    NMF_FMG = 2     /* Algorithm Full Multigrid (Section 4.3.3) */
+} nmf_cycle;
+
+typedef enum {
+    NMF_OK = 0,
+    NMF_EINVAL = -1,   /* bad argument: sizes, m != grid_h*grid_w, r out of range, negative or NaN entries */
+    NMF_ENOMEM = -2,   /* workspace would exceed the handle's HBM budget, or the device is out of memory */
+    NMF_ENOCONV = -3,  /* an ANLS active-set solve hit its iteration cap (results are the last iterate) */
+    NMF_ECUDA = -4,    /* a CUDA runtime call failed */
+    NMF_ETIMEOUT = -5, /* a bounded device-side wait gave up */
+    NMF_EBUSY = -6     /* serving queue full or request not finished */
+} nmf_status;
+
+/*
+ * nmf_create - open a handle on CUDA device `device`.
+ *   hbm_budget_bytes: upper bound on the device memory the handle may hold for
+ *     its workspaces (0 = no limit besides the device's).  Work that needs more
+ *     fails with NMF_ENOMEM before touching the device.
+ *   prec: storage precision used by nmf_solve on this handle.
+ *   *out receives the handle; release it with nmf_destroy.
+ */
+int nmf_create(nmf_handle* out, int device, size_t hbm_budget_bytes, nmf_precision prec);
+
+/* nmf_destroy - free every device resource of the handle (NULL is accepted). */
+void nmf_destroy(nmf_handle h);
+
+/* nmf_last_error - reason for the last failing call on h (static string if h is NULL). */
+const char* nmf_last_error(nmf_handle h);
+
+/* Options of nmf_solve_ex.  Zero-initialise and set what is needed. */
+typedef struct {
+    nmf_cycle cycle;      /* multigrid cycle (default NMF_VCYCLE) */
+    int64_t stop_after;   /* if > 0: run only the first stop_after sweeps of the schedule
+                             (the iterates are then exactly those of the full run at that point) */
+    double* trace;        /* optional host array: ||M - VW||_F after each sweep at the finest level,
+                             in schedule order; FP64 accumulation.  Costs one extra pass over M per
+                             fine sweep. */
+    int64_t trace_len;    /* capacity of trace; entries beyond it are not written */
+    int64_t* trace_count; /* optional: receives the number of fine-level sweeps run */
+} nmf_options;
+
+/*
+ * nmf_solve - multilevel NMF (Section 4): improves (V, W) in place.
+ *   M: m x n, M >= 0 (checked: NMF_EINVAL on a negative or NaN entry).
+ *   grid_h * grid_w must equal m; rows are pixels in row-major grid order.
+ *   r: factorisation rank, 1..64.
+ *   algo: inner algorithm; levels: number of grid levels L (1 = the plain
+ *   algorithm on the input grid); iters: sweep budget K.  With the reading of
+ *   Table 1 (Section 4.3) a V-cycle runs floor(K/4) pre-sweeps and floor(K/2)
+ *   post-sweeps on levels 1..L-1 and K sweeps on level L.
+ *   V (m x r) and W (r x n): in = initial iterate (>= 0), out = result.
+ * nmf_solve runs a V-cycle; nmf_solve_ex takes an nmf_options (NULL = defaults).
+ */
+int nmf_solve(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h, int grid_w,
+              int r, nmf_algo algo, int levels, int iters, float* V, float* W);
+int nmf_solve_ex(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h, int grid_w,
+                 int r, nmf_algo algo, int levels, int iters, const nmf_options* opt,
+                 float* V, float* W);
+
+/*
+ * nmf_error - ||M - VW||_F (problem (NMF), Section 2) with float32 products and
+ * FP64 accumulation of the squared residuals.  *err_out receives the value
+ * (host pointer).
+ */
+int nmf_error(nmf_handle h, const float* M, const float* V, const float* W,
+              int64_t m, int64_t n, int r, double* err_out);
+
+/*
+ * nmf_schedule - host-side sweep allocation of a cycle (no device work).
+ *   Writes the number of sweeps run on each level 1..levels into
+ *   sweeps_per_level[0..levels-1] (Table 1 of Section 4.3 for the V-cycle and
+ *   nested iteration; Algorithm FMG's recursion for NMF_FMG) and returns the
+ *   total, or a negative nmf_status.
+ */
+int64_t nmf_schedule(nmf_cycle cycle, int levels, int iters, int64_t* sweeps_per_level);
+
+/*
+ * nmf_restrict - Y = R X, the full-weighting restriction of Eq. (4.1) applied
+ * to each of the `cols` columns of X ((grid_h*grid_w) x cols).  Y is
+ * (ceil(grid_h/2)*ceil(grid_w/2)) x cols.  On the border the stencil keeps the
+ * in-bounds fine pixels and renormalises their weights to sum 1.
+ */
+int nmf_restrict(nmf_handle h, const float* X, int grid_h, int grid_w, int64_t cols, float* Y);
+
+/*
+ * nmf_prolong - X = P Y, the prolongation of Eq. (4.2) from the coarse grid
+ * (ceil(grid_h/2) x ceil(grid_w/2)) to the fine grid grid_h x grid_w, for each
+ * of the `cols` columns.  A fine pixel is the mean of its 1, 2 or 4 coarse
+ * neighbours (neighbours past an even-size border are dropped).
+ */
+int nmf_prolong(nmf_handle h, const float* Y, int grid_h, int grid_w, int64_t cols, float* X);
+
+/*
+ * nmf_products - the four dense products of one HALS/MU sweep (Section 2.3,
+ * Appendix A.1) with the library's GEMM kernels:
+ *   A = M W^T (m x r), B = W W^T (r x r), C = V^T M (r x n), D = V^T V (r x r).
+ * Any output pointer may be NULL to skip it.
+ */
+int nmf_products(nmf_handle h, const float* M, const float* V, const float* W,
+                 int64_t m, int64_t n, int r, float* A, float* B, float* C, float* D);
+
+/*
+ * nmf_sweep - `sweeps` iterations of the inner algorithm at a single level
+ * (no grid): identical to nmf_solve with levels = 1, grid m x 1.
+ */
+int nmf_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo,
+              int sweeps, float* V, float* W);
+
+/* nmf_device_info - number of SMs of the handle's device and the library's build tag. */
+int nmf_device_info(nmf_handle h, int* num_sms, const char** build_tag);
+
+/*
+ * nmf_set_stream - run the handle's work on `stream` (a cudaStream_t of the
+ * handle's device, passed as void*; NULL restores the handle's own stream).
+ * The caller keeps ownership of the stream.  Calls stay synchronous.
+ */
+int nmf_set_stream(nmf_handle h, void* stream);
+
+/*
+ * nmf_last_launch_count - number of kernels the last successful call on h
+ * launched (graph kernel nodes included), or a negative nmf_status.
+ */
+int64_t nmf_last_launch_count(nmf_handle h);
+
+/*
+ * nmf_profile_sweep - per-kernel timing of one sweep at a single level:
+ * each phase is launched `reps` times on the handle's stream between CUDA
+ * events, and ms_out[i] receives the mean duration of one launch, in order:
+ *   [0] products for the V-step (A = M W^T and B = W W^T, one launch)
+ *   [1] V-step update        [2] products for the W-step (C = V^T M, D = V^T V)
+ *   [3] W-step update        [4] error evaluation ||M - VW||_F
+ * M, V, W as in nmf_sweep; they are read only (the library works on copies).
+ */
+int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo,
+                      const float* V, const float* W, int reps, float* ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_NMF_H */

@@ -1,0 +1,854 @@
+// Host driver and C ABI (include/nmf.h).
+//
+// A solve is planned once (level hierarchy of Section 4.2, workspace layout,
+// split-K plan of every product), its whole multigrid schedule (Section 4.3)
+// is recorded into one CUDA graph, and the graph is cached on the handle and
+// replayed for later solves of the same shape.  Only the staging of caller
+// buffers and the final status read cross the host/device boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "nmf_internal.cuh"
+
+using namespace nmfk;
+
+namespace {
+
+const char* kBuildTag = "gb300-nmf sm_103a fp32-ffma";
+
+// ---------------------------------------------------------------------------
+// Cycle schedules (Section 4.3) as a flat list of operations
+// ---------------------------------------------------------------------------
+enum OpKind { OP_SWEEPS = 0, OP_RESTRICT_V = 1, OP_PROLONG_V = 2 };
+struct Op {
+    OpKind kind;
+    int level;  // 0 = finest
+    int64_t count;
+};
+
+struct ScheduleBuilder {
+    std::vector<Op> ops;
+    void sweeps(int lvl, int64_t c) {
+        if (c > 0) ops.push_back({OP_SWEEPS, lvl, c});
+    }
+    // Algorithm V-cycle: floor(K/4) pre-sweeps, coarse V-cycle with the same K
+    // (a quarter of the time on a level four times cheaper), prolongation,
+    // floor(K/2) post-sweeps; K sweeps on the coarsest level (Table 1).
+    void vcycle(int lvl, int L, int64_t K) {
+        if (L == 1) {
+            sweeps(lvl, K);
+            return;
+        }
+        sweeps(lvl, K / 4);
+        ops.push_back({OP_RESTRICT_V, lvl, 0});
+        vcycle(lvl + 1, L - 1, K);
+        ops.push_back({OP_PROLONG_V, lvl, 0});
+        sweeps(lvl, K / 2);
+    }
+    // Algorithm Nested Iteration: coarse solve (budget K), prolong, floor(3K/4) sweeps.
+    void nested(int lvl, int L, int64_t K) {
+        if (L == 1) {
+            sweeps(lvl, K);
+            return;
+        }
+        ops.push_back({OP_RESTRICT_V, lvl, 0});
+        nested(lvl + 1, L - 1, K);
+        ops.push_back({OP_PROLONG_V, lvl, 0});
+        sweeps(lvl, (3 * K) / 4);
+    }
+    // Algorithm Full Multigrid: FMG on the coarser level (budget K), prolong,
+    // then a V-cycle over the L levels with budget floor(3K/4).
+    void fmg(int lvl, int L, int64_t K) {
+        if (L == 1) {
+            sweeps(lvl, K);
+            return;
+        }
+        ops.push_back({OP_RESTRICT_V, lvl, 0});
+        fmg(lvl + 1, L - 1, K);
+        ops.push_back({OP_PROLONG_V, lvl, 0});
+        vcycle(lvl, L, (3 * K) / 4);
+    }
+};
+
+std::vector<Op> build_schedule(nmf_cycle cyc, int L, int64_t K) {
+    ScheduleBuilder b;
+    if (cyc == NMF_NESTED)
+        b.nested(0, L, K);
+    else if (cyc == NMF_FMG)
+        b.fmg(0, L, K);
+    else
+        b.vcycle(0, L, K);
+    return b.ops;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+struct Bump {
+    char* base = nullptr;
+    size_t off = 0, cap = 0;
+    bool dry = true;
+    template <typename T>
+    T* take(size_t count) {
+        off = (size_t)round_up((int64_t)off, 256);
+        T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+struct Level {
+    int h = 0, w = 0;
+    int64_t m = 0;
+    float* M = nullptr;   // m x ldm
+    float* Mt = nullptr;  // n x ldmt
+    int64_t ldmt = 0;
+    float* V = nullptr;  // m x rp
+    GemmTask tA{}, tB{}, tC{}, tD{};
+};
+
+struct Plan {
+    int64_t m = 0, n = 0, ldm = 0;
+    int r = 0, rp = 0, br = 0, L = 1;
+    std::vector<Level> lv;
+    float* Wt = nullptr;
+    float* P1 = nullptr;  // A partials
+    float* PG1 = nullptr; // B partials
+    float* P2 = nullptr;  // C^T partials
+    float* PG2 = nullptr; // D partials
+    float* tmp = nullptr; // r x n staging for W
+    double* err_part = nullptr;
+    double* err_out = nullptr;
+    double* d_trace = nullptr;
+    int* d_status = nullptr;
+    unsigned long long* d_bad = nullptr;
+    int64_t trace_cap = 0;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;      // kernel nodes per replay
+    int64_t fine_sweeps = 0;  // finest-level sweeps per replay
+};
+
+struct nmf_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;      // stream in use
+    cudaStream_t own_stream = nullptr;  // stream created with the handle
+    int64_t launches = 0;               // kernels launched by the current/last call
+    size_t budget = 0;
+    nmf_precision prec = NMF_FP32;
+    std::string err;
+    char* ws = nullptr;
+    size_t ws_cap = 0;
+    // pinned host scalars
+    unsigned long long* h_bad = nullptr;
+    int* h_status = nullptr;
+    double* h_err = nullptr;
+    std::map<std::string, GraphEntry> graphs;
+};
+
+namespace {
+
+int fail(nmf_ctx* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    return code;
+}
+
+#define CK(expr)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? NMF_ENOMEM : NMF_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+    } while (0)
+
+// CK for a kernel launch helper that launches `n` kernels (counted on the handle)
+#define KL(n, expr)           \
+    do {                      \
+        CK(expr);             \
+        h->launches += (n);   \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int pick_br(int rp) {
+    if (rp <= 16) return 16;
+    if (rp <= 32) return 32;
+    if (rp <= 48) return 48;
+    return 64;
+}
+
+constexpr int kMaxSplits = 32;
+
+// Lay out (or size, when b.dry) the workspace of a solve.
+void layout(Plan& p, Bump& b, int num_sms) {
+    const int64_t n = p.n, rp = p.rp;
+    int64_t max_p1 = 0, max_p2 = 0, max_pg1 = 0, max_pg2 = 0;
+    for (int l = 0; l < p.L; ++l) {
+        Level& v = p.lv[l];
+        v.ldmt = round_up(v.m, 4);
+        v.M = b.take<float>((size_t)(v.m * p.ldm));
+        v.Mt = b.take<float>((size_t)(n * v.ldmt));
+        v.V = b.take<float>((size_t)(v.m * rp));
+        // A = M W^T: X = Mt (K = n), Y = Wt
+        v.tA = GemmTask{};
+        v.tA.Na = (int)v.m;
+        v.tA.K = n;
+        v.tA.ldx = v.ldmt;
+        v.tA.ldy = rp;
+        v.tA.ldo = rp;
+        gemm_plan_task(v.tA, num_sms, kMaxSplits);
+        v.tA.split_stride = v.m * rp;
+        // B = W W^T: X = Y = Wt
+        v.tB = GemmTask{};
+        v.tB.Na = p.r;
+        v.tB.K = n;
+        v.tB.ldx = rp;
+        v.tB.ldy = rp;
+        v.tB.ldo = rp;
+        gemm_plan_task(v.tB, num_sms, kMaxSplits);
+        v.tB.split_stride = (int64_t)p.r * rp;
+        // C^T = M^T V: X = M (K = m), Y = V
+        v.tC = GemmTask{};
+        v.tC.Na = (int)n;
+        v.tC.K = v.m;
+        v.tC.ldx = p.ldm;
+        v.tC.ldy = rp;
+        v.tC.ldo = rp;
+        gemm_plan_task(v.tC, num_sms, kMaxSplits);
+        v.tC.split_stride = n * rp;
+        // D = V^T V
+        v.tD = GemmTask{};
+        v.tD.Na = p.r;
+        v.tD.K = v.m;
+        v.tD.ldx = rp;
+        v.tD.ldy = rp;
+        v.tD.ldo = rp;
+        gemm_plan_task(v.tD, num_sms, kMaxSplits);
+        v.tD.split_stride = (int64_t)p.r * rp;
+        max_p1 = std::max<int64_t>(max_p1, v.tA.splits * v.tA.split_stride);
+        max_pg1 = std::max<int64_t>(max_pg1, v.tB.splits * v.tB.split_stride);
+        max_p2 = std::max<int64_t>(max_p2, v.tC.splits * v.tC.split_stride);
+        max_pg2 = std::max<int64_t>(max_pg2, v.tD.splits * v.tD.split_stride);
+    }
+    p.Wt = b.take<float>((size_t)(n * rp));
+    p.P1 = b.take<float>((size_t)max_p1);
+    p.PG1 = b.take<float>((size_t)max_pg1);
+    p.P2 = b.take<float>((size_t)max_p2);
+    p.PG2 = b.take<float>((size_t)max_pg2);
+    p.tmp = b.take<float>((size_t)std::max<int64_t>(std::max<int64_t>(p.r * n, n * rp), p.lv[0].m * rp));
+    p.err_part = b.take<double>((size_t)error_partials_needed(p.lv[0].m, n));
+    p.err_out = b.take<double>(1);
+    p.d_trace = b.take<double>((size_t)(p.trace_cap > 0 ? p.trace_cap : 1));
+    p.d_status = b.take<int>(1);
+    p.d_bad = b.take<unsigned long long>(1);
+    for (int l = 0; l < p.L; ++l) {
+        Level& v = p.lv[l];
+        v.tA.X = v.Mt;
+        v.tA.Y = p.Wt;
+        v.tA.out = p.P1;
+        v.tB.X = p.Wt;
+        v.tB.Y = p.Wt;
+        v.tB.out = p.PG1;
+        v.tC.X = v.M;
+        v.tC.Y = v.V;
+        v.tC.out = p.P2;
+        v.tD.X = v.V;
+        v.tD.Y = v.V;
+        v.tD.out = p.PG2;
+    }
+    p.bytes = b.off;
+}
+
+int ensure_workspace(nmf_ctx* h, size_t bytes) {
+    if (h->budget && bytes > h->budget)
+        return fail(h, NMF_ENOMEM, "workspace of %zu bytes exceeds the HBM budget of %zu bytes", bytes, h->budget);
+    if (bytes <= h->ws_cap) return NMF_OK;
+    // new workspace: graphs recorded against the old one are stale
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_cap = 0;
+    cudaError_t e = cudaMalloc(&h->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->ws = nullptr;
+        return fail(h, NMF_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    h->ws_cap = bytes;
+    return NMF_OK;
+}
+
+int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap) {
+    p.m = m;
+    p.n = n;
+    p.r = r;
+    p.rp = (int)round_up(r, 4);
+    p.br = pick_br(p.rp);
+    p.L = L;
+    p.ldm = round_up(n, 4);
+    p.trace_cap = trace_cap;
+    p.lv.assign(L, Level{});
+    int hh = gh, ww = gw;
+    for (int l = 0; l < L; ++l) {
+        p.lv[l].h = hh;
+        p.lv[l].w = ww;
+        p.lv[l].m = (int64_t)hh * ww;
+        hh = (hh + 1) / 2;
+        ww = (ww + 1) / 2;
+    }
+    Bump dry;
+    layout(p, dry, h->num_sms);
+    int rc = ensure_workspace(h, dry.off);
+    if (rc) return rc;
+    Bump real;
+    real.dry = false;
+    real.base = h->ws;
+    real.cap = h->ws_cap;
+    layout(p, real, h->num_sms);
+    return NMF_OK;
+}
+
+UpdateArgs v_update_args(const Plan& p, const Level& v) {
+    UpdateArgs u{};
+    u.F = v.V;
+    u.ldf = p.rp;
+    u.P = p.P1;
+    u.ps = v.tA.split_stride;
+    u.ldp = p.rp;
+    u.splits = v.tA.splits;
+    u.PG = p.PG1;
+    u.pgs = v.tB.split_stride;
+    u.ldpg = p.rp;
+    u.gsplits = v.tB.splits;
+    u.rows = v.m;
+    u.r = p.r;
+    return u;
+}
+
+UpdateArgs w_update_args(const Plan& p, const Level& v) {
+    UpdateArgs u{};
+    u.F = p.Wt;
+    u.ldf = p.rp;
+    u.P = p.P2;
+    u.ps = v.tC.split_stride;
+    u.ldp = p.rp;
+    u.splits = v.tC.splits;
+    u.PG = p.PG2;
+    u.pgs = v.tD.split_stride;
+    u.ldpg = p.rp;
+    u.gsplits = v.tD.splits;
+    u.rows = p.n;
+    u.r = p.r;
+    return u;
+}
+
+cudaError_t run_update(nmf_ctx* h, const Plan& p, const UpdateArgs& u, nmf_algo algo) {
+    switch (algo) {
+        case NMF_HALS: return hals_update_launch(u, h->num_sms, h->stream);
+        case NMF_MU: return mu_update_launch(u, h->num_sms, h->stream);
+        default: return anls_update_launch(u, h->num_sms, p.d_status, h->stream);
+    }
+}
+
+// One sweep of the inner algorithm at level l: products for the V-step, V-step,
+// products for the W-step (with the new V), W-step.
+cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo) {
+    const Level& v = p.lv[l];
+    GemmBatch b1{};
+    b1.t[0] = v.tA;
+    b1.t[1] = v.tB;
+    b1.ntasks = 2;
+    cudaError_t e = gemm_tn_launch(b1, p.br, h->stream);
+    if (e != cudaSuccess) return e;
+    e = run_update(h, p, v_update_args(p, v), algo);
+    if (e != cudaSuccess) return e;
+    GemmBatch b2{};
+    b2.t[0] = v.tC;
+    b2.t[1] = v.tD;
+    b2.ntasks = 2;
+    e = gemm_tn_launch(b2, p.br, h->stream);
+    if (e != cudaSuccess) return e;
+    return run_update(h, p, w_update_args(p, v), algo);
+}
+
+// Restrictions of M for every level (computed once per solve, footnote of
+// Algorithm FMG) and the transposed copies.
+cudaError_t enqueue_hierarchy(nmf_ctx* h, const Plan& p) {
+    for (int l = 0; l + 1 < p.L; ++l) {
+        const Level& f = p.lv[l];
+        const Level& c = p.lv[l + 1];
+        cudaError_t e = restrict_launch(f.M, p.ldm, f.h, f.w, p.ldm, c.M, p.ldm, h->stream);
+        if (e != cudaSuccess) return e;
+        e = copy2d_launch(c.M, p.ldm, c.m, p.n, c.Mt, c.ldmt, true, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& ops, nmf_algo algo,
+                             int64_t stop_after, bool trace, int64_t* fine_sweeps) {
+    int64_t done = 0, tidx = 0;
+    cudaError_t e = cudaSuccess;
+    for (const Op& op : ops) {
+        const Level& f = p.lv[op.level];
+        if (op.kind == OP_RESTRICT_V) {
+            const Level& c = p.lv[op.level + 1];
+            e = restrict_launch(f.V, p.rp, f.h, f.w, p.rp, c.V, p.rp, h->stream);
+        } else if (op.kind == OP_PROLONG_V) {
+            const Level& c = p.lv[op.level + 1];
+            e = prolong_launch(c.V, p.rp, f.h, f.w, p.rp, f.V, p.rp, h->stream);
+        } else {
+            for (int64_t s = 0; s < op.count; ++s) {
+                if (stop_after > 0 && done >= stop_after) break;
+                e = enqueue_sweep(h, p, op.level, algo);
+                if (e != cudaSuccess) return e;
+                ++done;
+                if (op.level == 0) {
+                    if (trace && tidx < p.trace_cap) {
+                        e = error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, f.m, p.n, p.r, p.err_part, p.d_trace + tidx,
+                                         h->stream);
+                        if (e != cudaSuccess) return e;
+                    }
+                    ++tidx;
+                }
+            }
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (fine_sweeps) *fine_sweeps = tidx;
+    return cudaSuccess;
+}
+
+// Copy a caller matrix (host or device, rows x cols, dense) into a padded
+// device buffer (rows x ld).
+cudaError_t stage_in(nmf_ctx* h, const float* src, int64_t rows, int64_t cols, float* dst, int64_t ld) {
+    const cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (ld != cols) {
+        cudaError_t e = cudaMemsetAsync(dst, 0, sizeof(float) * rows * ld, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaMemcpy2DAsync(dst, sizeof(float) * ld, src, sizeof(float) * cols, sizeof(float) * cols, rows, kind,
+                             h->stream);
+}
+
+cudaError_t stage_out(nmf_ctx* h, const float* src, int64_t ld, int64_t rows, int64_t cols, float* dst) {
+    const cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    return cudaMemcpy2DAsync(dst, sizeof(float) * cols, src, sizeof(float) * ld, sizeof(float) * cols, rows, kind,
+                             h->stream);
+}
+
+int check_dims(nmf_ctx* h, int64_t m, int64_t n, int r) {
+    if (m < 1 || n < 1) return fail(h, NMF_EINVAL, "m and n must be >= 1 (got %lld, %lld)", (long long)m, (long long)n);
+    if (r < 1 || r > kMaxRank) return fail(h, NMF_EINVAL, "r must be in 1..%d (got %d)", kMaxRank, r);
+    if (n > (1LL << 31) - 64 || m > (1LL << 31) - 64) return fail(h, NMF_EINVAL, "m, n must be < 2^31");
+    return NMF_OK;
+}
+
+// Stage M, V0, W0 into level 0 of the plan and validate them on the device.
+int stage_problem(nmf_ctx* h, Plan& p, const float* M, const float* V, const float* W) {
+    Level& f = p.lv[0];
+    CK(stage_in(h, M, p.m, p.n, f.M, p.ldm));
+    KL(1, copy2d_launch(f.M, p.ldm, p.m, p.n, f.Mt, f.ldmt, true, h->stream));
+    if (f.ldmt != p.m) {
+        // zero the padding columns of Mt (rows of the transpose beyond m)
+        CK(cudaMemset2DAsync(f.Mt + p.m, sizeof(float) * f.ldmt, 0, sizeof(float) * (f.ldmt - p.m), p.n, h->stream));
+    }
+    if (V) CK(stage_in(h, V, p.m, p.r, f.V, p.rp));
+    if (W) {
+        CK(stage_in(h, W, p.r, p.n, p.tmp, p.n));
+        CK(cudaMemsetAsync(p.Wt, 0, sizeof(float) * p.n * p.rp, h->stream));
+        KL(1, copy2d_launch(p.tmp, p.n, p.r, p.n, p.Wt, p.rp, true, h->stream));
+    }
+    CK(cudaMemsetAsync(p.d_bad, 0, sizeof(unsigned long long), h->stream));
+    KL(1, check_nonneg_launch(f.M, p.ldm, p.m, p.n, p.d_bad, h->stream));
+    if (V) KL(1, check_nonneg_launch(f.V, p.rp, p.m, p.r, p.d_bad, h->stream));
+    if (W) KL(1, check_nonneg_launch(p.Wt, p.rp, p.n, p.r, p.d_bad, h->stream));
+    return NMF_OK;
+}
+
+int init_levels_padding(nmf_ctx* h, Plan& p) {
+    // coarse-level buffers: zero once so padding columns are zero
+    for (int l = 1; l < p.L; ++l) {
+        Level& v = p.lv[l];
+        CK(cudaMemsetAsync(v.M, 0, sizeof(float) * v.m * p.ldm, h->stream));
+        CK(cudaMemsetAsync(v.Mt, 0, sizeof(float) * p.n * v.ldmt, h->stream));
+        CK(cudaMemsetAsync(v.V, 0, sizeof(float) * v.m * p.rp, h->stream));
+    }
+    return NMF_OK;
+}
+
+int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw, int r, nmf_algo algo, int L,
+               int K, const nmf_options* opt, float* V, float* W) {
+    if (!h) return NMF_EINVAL;
+    int rc = check_dims(h, m, n, r);
+    if (rc) return rc;
+    if (!M || !V || !W) return fail(h, NMF_EINVAL, "M, V and W must be non-null");
+    if (gh < 1 || gw < 1 || (int64_t)gh * gw != m)
+        return fail(h, NMF_EINVAL, "grid %d x %d does not have m = %lld pixels", gh, gw, (long long)m);
+    if (L < 1 || L > 16) return fail(h, NMF_EINVAL, "levels must be in 1..16 (got %d)", L);
+    if (K < 0) return fail(h, NMF_EINVAL, "iters must be >= 0");
+    if (algo != NMF_HALS && algo != NMF_MU && algo != NMF_ANLS) return fail(h, NMF_EINVAL, "unknown algorithm");
+    const nmf_cycle cyc = opt ? opt->cycle : NMF_VCYCLE;
+    if (cyc != NMF_VCYCLE && cyc != NMF_NESTED && cyc != NMF_FMG) return fail(h, NMF_EINVAL, "unknown cycle");
+    const int64_t stop_after = opt ? opt->stop_after : 0;
+    const bool trace = opt && opt->trace && opt->trace_len > 0;
+    if (h->prec != NMF_FP32) return fail(h, NMF_EINVAL, "only the FP32 storage precision is built");
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+
+    Plan p;
+    rc = make_plan(h, p, m, n, gh, gw, r, L, trace ? opt->trace_len : 0);
+    if (rc) return rc;
+    rc = init_levels_padding(h, p);
+    if (rc) return rc;
+    rc = stage_problem(h, p, M, V, W);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
+    CK(cudaMemcpyAsync(h->h_bad, p.d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+
+    // the whole hierarchy + schedule as one cached CUDA graph
+    char key[256];
+    snprintf(key, sizeof key, "solve:%lld:%lld:%d:%d:%d:%d:%d:%d:%d:%lld:%lld:%p", (long long)m, (long long)n, gh, gw,
+             r, (int)algo, L, K, (int)cyc, (long long)stop_after, (long long)(trace ? opt->trace_len : 0),
+             (void*)h->ws);
+    const std::vector<Op> ops = build_schedule(cyc, L, K);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        GraphEntry ge;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_hierarchy(h, p);
+        if (e == cudaSuccess) e = enqueue_schedule(h, p, ops, algo, stop_after, trace, &ge.fine_sweeps);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(h, NMF_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        size_t nn = 0;
+        e = cudaGraphGetNodes(graph, nullptr, &nn);
+        if (e == cudaSuccess && nn) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+            for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++ge.kernels;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(h, NMF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        it = h->graphs.emplace(key, ge).first;
+    }
+    const GraphEntry& ge = it->second;
+    const cudaGraphExec_t exec = ge.exec;
+    const int64_t fine_sweeps = ge.fine_sweeps;
+    h->launches += ge.kernels;
+    CK(cudaGraphLaunch(exec, h->stream));
+    CK(cudaMemcpyAsync(h->h_status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (*h->h_bad) return fail(h, NMF_EINVAL, "%llu negative, NaN or infinite entries in M, V0 or W0", *h->h_bad);
+
+    // results back to the caller's layout
+    const Level& f = p.lv[0];
+    CK(stage_out(h, f.V, p.rp, m, r, V));
+    KL(1, copy2d_launch(p.Wt, p.rp, n, r, p.tmp, n, true, h->stream));
+    CK(stage_out(h, p.tmp, n, r, n, W));
+    if (trace) {
+        const int64_t cnt = std::min<int64_t>(fine_sweeps, opt->trace_len);
+        if (cnt > 0) CK(cudaMemcpyAsync(opt->trace, p.d_trace, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (opt && opt->trace_count) *opt->trace_count = fine_sweeps;
+    if (*h->h_status) return fail(h, NMF_ENOCONV, "an active-set NNLS solve reached its iteration cap");
+    return NMF_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int nmf_create(nmf_handle* out, int device, size_t hbm_budget_bytes, nmf_precision prec) {
+    if (!out) return NMF_EINVAL;
+    *out = nullptr;
+    if (prec != NMF_FP32 && prec != NMF_BF16) return NMF_EINVAL;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return NMF_ECUDA;
+    }
+    nmf_ctx* h = new nmf_ctx;
+    h->device = device;
+    h->budget = hbm_budget_bytes;
+    h->prec = prec;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&h->h_bad, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&h->h_err, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        nmf_destroy(h);
+        return NMF_ECUDA;
+    }
+    h->stream = h->own_stream;
+    if (init_kernel_attributes() != cudaSuccess) {
+        cudaGetLastError();
+        nmf_destroy(h);
+        return NMF_ECUDA;
+    }
+    *out = h;
+    return NMF_OK;
+}
+
+void nmf_destroy(nmf_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+    if (h->ws) cudaFree(h->ws);
+    if (h->h_bad) cudaFreeHost(h->h_bad);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+const char* nmf_last_error(nmf_handle h) {
+    if (!h) return "invalid handle";
+    return h->err.c_str();
+}
+
+int64_t nmf_schedule(nmf_cycle cycle, int levels, int iters, int64_t* sweeps_per_level) {
+    if (levels < 1 || levels > 16 || iters < 0) return NMF_EINVAL;
+    if (cycle != NMF_VCYCLE && cycle != NMF_NESTED && cycle != NMF_FMG) return NMF_EINVAL;
+    std::vector<Op> ops = build_schedule(cycle, levels, iters);
+    int64_t total = 0;
+    if (sweeps_per_level)
+        for (int l = 0; l < levels; ++l) sweeps_per_level[l] = 0;
+    for (const Op& op : ops)
+        if (op.kind == OP_SWEEPS) {
+            total += op.count;
+            if (sweeps_per_level) sweeps_per_level[op.level] += op.count;
+        }
+    return total;
+}
+
+int nmf_solve(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h, int grid_w, int r, nmf_algo algo,
+              int levels, int iters, float* V, float* W) {
+    return solve_impl(h, M, m, n, grid_h, grid_w, r, algo, levels, iters, nullptr, V, W);
+}
+
+int nmf_solve_ex(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h, int grid_w, int r, nmf_algo algo,
+                 int levels, int iters, const nmf_options* opt, float* V, float* W) {
+    return solve_impl(h, M, m, n, grid_h, grid_w, r, algo, levels, iters, opt, V, W);
+}
+
+int nmf_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo, int sweeps, float* V,
+              float* W) {
+    if (m > (1LL << 31) - 64) return fail(h, NMF_EINVAL, "m too large");
+    return solve_impl(h, M, m, n, (int)m, 1, r, algo, 1, sweeps, nullptr, V, W);
+}
+
+int nmf_error(nmf_handle h, const float* M, const float* V, const float* W, int64_t m, int64_t n, int r,
+              double* err_out) {
+    if (!h) return NMF_EINVAL;
+    int rc = check_dims(h, m, n, r);
+    if (rc) return rc;
+    if (!M || !V || !W || !err_out) return fail(h, NMF_EINVAL, "null argument");
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+    Plan p;
+    rc = make_plan(h, p, m, n, (int)m, 1, r, 1, 0);
+    if (rc) return rc;
+    rc = stage_problem(h, p, M, V, W);
+    if (rc) return rc;
+    const Level& f = p.lv[0];
+    KL(2, error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, m, n, r, p.err_part, p.err_out, h->stream));
+    CK(cudaMemcpyAsync(h->h_err, p.err_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *err_out = sqrt(*h->h_err);
+    return NMF_OK;
+}
+
+int nmf_products(nmf_handle h, const float* M, const float* V, const float* W, int64_t m, int64_t n, int r,
+                 float* A, float* B, float* C, float* D) {
+    if (!h) return NMF_EINVAL;
+    int rc = check_dims(h, m, n, r);
+    if (rc) return rc;
+    if (!M || !V || !W) return fail(h, NMF_EINVAL, "null argument");
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+    Plan p;
+    rc = make_plan(h, p, m, n, (int)m, 1, r, 1, 0);
+    if (rc) return rc;
+    rc = stage_problem(h, p, M, V, W);
+    if (rc) return rc;
+    const Level& v = p.lv[0];
+    GemmBatch b1{};
+    b1.t[0] = v.tA;
+    b1.t[1] = v.tB;
+    b1.ntasks = 2;
+    KL(1, gemm_tn_launch(b1, p.br, h->stream));
+    GemmBatch b2{};
+    b2.t[0] = v.tC;
+    b2.t[1] = v.tD;
+    b2.ntasks = 2;
+    KL(1, gemm_tn_launch(b2, p.br, h->stream));
+    // reduce the split-K slabs into dense outputs, staged through tmp
+    struct Out {
+        float* dst;
+        const float* P;
+        int64_t ps;
+        int splits;
+        int64_t rows, cols;
+        bool transpose;
+    } outs[4] = {{A, p.P1, v.tA.split_stride, v.tA.splits, m, r, false},
+                 {B, p.PG1, v.tB.split_stride, v.tB.splits, r, r, false},
+                 {C, p.P2, v.tC.split_stride, v.tC.splits, n, r, true},
+                 {D, p.PG2, v.tD.split_stride, v.tD.splits, r, r, false}};
+    for (const Out& o : outs) {
+        if (!o.dst) continue;
+        const int64_t orow = o.transpose ? o.cols : o.rows, ocol = o.transpose ? o.rows : o.cols;
+        KL(1, sum_splits_launch(o.P, o.ps, p.rp, o.splits, o.rows, o.cols, p.tmp, ocol, o.transpose, h->stream));
+        CK(stage_out(h, p.tmp, ocol, orow, ocol, o.dst));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return NMF_OK;
+}
+
+static int transfer_impl(nmf_handle h, const float* in, int gh, int gw, int64_t cols, float* out, bool restrict_op) {
+    if (!h) return NMF_EINVAL;
+    if (!in || !out || gh < 1 || gw < 1 || cols < 1) return fail(h, NMF_EINVAL, "bad transfer arguments");
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+    const int64_t mf = (int64_t)gh * gw, mc = (int64_t)((gh + 1) / 2) * ((gw + 1) / 2);
+    const int64_t rows_in = restrict_op ? mf : mc, rows_out = restrict_op ? mc : mf;
+    const int64_t ld = round_up(cols, 4);
+    const size_t bytes = sizeof(float) * (size_t)(round_up(rows_in * ld, 64) + round_up(rows_out * ld, 64)) + 512;
+    int rc = ensure_workspace(h, bytes);
+    if (rc) return rc;
+    float* bin = reinterpret_cast<float*>(h->ws);
+    float* bout = bin + round_up(rows_in * ld, 64);
+    CK(stage_in(h, in, rows_in, cols, bin, ld));
+    if (restrict_op)
+        KL(1, restrict_launch(bin, ld, gh, gw, cols, bout, ld, h->stream));
+    else
+        KL(1, prolong_launch(bin, ld, gh, gw, cols, bout, ld, h->stream));
+    CK(stage_out(h, bout, ld, rows_out, cols, out));
+    CK(cudaStreamSynchronize(h->stream));
+    return NMF_OK;
+}
+
+int nmf_restrict(nmf_handle h, const float* X, int grid_h, int grid_w, int64_t cols, float* Y) {
+    return transfer_impl(h, X, grid_h, grid_w, cols, Y, true);
+}
+
+int nmf_prolong(nmf_handle h, const float* Y, int grid_h, int grid_w, int64_t cols, float* X) {
+    return transfer_impl(h, Y, grid_h, grid_w, cols, X, false);
+}
+
+int nmf_device_info(nmf_handle h, int* num_sms, const char** build_tag) {
+    if (!h) return NMF_EINVAL;
+    if (num_sms) *num_sms = h->num_sms;
+    if (build_tag) *build_tag = kBuildTag;
+    return NMF_OK;
+}
+
+int nmf_set_stream(nmf_handle h, void* stream) {
+    if (!h) return NMF_EINVAL;
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
+    return NMF_OK;
+}
+
+int64_t nmf_last_launch_count(nmf_handle h) {
+    if (!h) return NMF_EINVAL;
+    return h->launches;
+}
+
+int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo, const float* V,
+                      const float* W, int reps, float* ms_out) {
+    if (!h) return NMF_EINVAL;
+    int rc = check_dims(h, m, n, r);
+    if (rc) return rc;
+    if (!M || !V || !W || !ms_out || reps < 1) return fail(h, NMF_EINVAL, "bad profile arguments");
+    if (algo != NMF_HALS && algo != NMF_MU && algo != NMF_ANLS) return fail(h, NMF_EINVAL, "unknown algorithm");
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+    Plan p;
+    rc = make_plan(h, p, m, n, (int)m, 1, r, 1, 0);
+    if (rc) return rc;
+    rc = stage_problem(h, p, M, V, W);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
+    const Level& v = p.lv[0];
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int out_rc = NMF_OK;
+    for (int phase = 0; phase < 5 && out_rc == NMF_OK; ++phase) {
+        // one untimed launch first so every phase starts from warm caches and valid inputs
+        for (int it = -1; it < reps; ++it) {
+            if (it == 0) cudaEventRecord(e0, h->stream);
+            cudaError_t e = cudaSuccess;
+            if (phase == 0 || phase == 2) {
+                GemmBatch b{};
+                b.t[0] = phase == 0 ? v.tA : v.tC;
+                b.t[1] = phase == 0 ? v.tB : v.tD;
+                b.ntasks = 2;
+                e = gemm_tn_launch(b, p.br, h->stream);
+            } else if (phase == 1) {
+                e = run_update(h, p, v_update_args(p, v), algo);
+            } else if (phase == 3) {
+                e = run_update(h, p, w_update_args(p, v), algo);
+            } else {
+                e = error_launch(v.M, p.ldm, v.V, p.Wt, p.rp, m, n, r, p.err_part, p.err_out, h->stream);
+            }
+            if (e != cudaSuccess) {
+                out_rc = fail(h, NMF_ECUDA, "profile launch failed: %s", cudaGetErrorString(e));
+                break;
+            }
+            h->launches += (phase == 4) ? 2 : 1;
+        }
+        if (out_rc != NMF_OK) break;
+        cudaEventRecord(e1, h->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) out_rc = fail(h, NMF_ECUDA, "profile timing failed: %s", cudaGetErrorString(e));
+        ms_out[phase] = ms / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return out_rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,427 @@
+// Row-parallel factor updates of the three inner NMF algorithms.
+//
+// The V-step updates the rows of V from (A = M W^T, B = W W^T); the W-step
+// updates the rows of Wt = W^T from (C^T = M^T V, D = V^T V).  Both steps act
+// on independent rows of a tall factor F with an r x r Gram matrix G, so one
+// kernel serves both.  Products arrive as split-K partial slabs and are summed
+// here in a fixed order (deterministic results).
+//
+// HALS (Algorithm HALS, Section 2.3).  Row i of F is updated column by column,
+// k = 1..r, in Gauss-Seidel order:
+//     F_ik <- max(0, (P_ik - sum_{l != k} F_il G_lk) / G_kk).
+// With g = P_i - F_i G kept up to date, the same value is F_ik + g_k / G_kk, and
+// after F_ik moves by delta every g_j drops by delta * G_kj.  The sequential
+// chain is then one division and one broadcast per k; the r-long dot products
+// of the formula become r independent FMAs spread over the lanes.
+// A group of 8 lanes owns one row (lane s holds entries k = s, s+8, ...), so a
+// warp updates 4 rows at once; G lives in shared memory.
+//
+// MU (Algorithm MU, Section 2.2): F <- F o P / max(F G, 1e-30), entrywise.
+//
+// ANLS (Algorithm ANLS, Section 2.1; Appendix A.2): each row solves
+//     min_{x >= 0} 1/2 x^T G x - P_i x
+// by the Lawson-Hanson active-set method in FP64 (Gram, right-hand side and
+// Cholesky factorisations of the passive block), one warp per row.
+#include "nmf_internal.cuh"
+
+namespace nmfk {
+
+namespace {
+
+constexpr int kLanesPerRow = 8;
+constexpr int kSlots = kMaxRank / kLanesPerRow;  // entries per lane
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kMuEps = 1e-30f;
+
+// Sum the Gram partial slabs into shared memory (row-major r x r).
+template <typename T>
+__device__ void reduce_gram(const UpdateArgs& u, T* G) {
+    const int r = u.r;
+    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+        const int l = idx / r, k = idx - l * r;
+        const float* p = u.PG + (int64_t)l * u.ldpg + k;
+        T s = 0;
+        for (int q = 0; q < u.gsplits; ++q) s += (T)p[(int64_t)q * u.pgs];
+        G[idx] = s;
+    }
+    __syncthreads();
+}
+
+template <bool kHals>
+__global__ void __launch_bounds__(256) rows_update_kernel(const UpdateArgs u) {
+    extern __shared__ float Gs[];
+    reduce_gram<float>(u, Gs);
+    const int r = u.r;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (kLanesPerRow - 1);
+    const int gbase = lane & ~(kLanesPerRow - 1);
+    const int warp = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const int rows_per_warp = 32 / kLanesPerRow;
+
+    for (int64_t base = ((int64_t)blockIdx.x * warps + warp) * rows_per_warp; base < u.rows;
+         base += (int64_t)gridDim.x * warps * rows_per_warp) {
+        const int64_t row = base + (lane / kLanesPerRow);
+        const bool active = row < u.rows;
+        float f[kSlots], g[kSlots];
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) {
+            const int k = sub + kLanesPerRow * j;
+            f[j] = 0.f;
+            g[j] = 0.f;
+            if (active && k < r) {
+                f[j] = u.F[row * u.ldf + k];
+                const float* p = u.P + row * u.ldp + k;
+                float s = 0.f;
+                for (int q = 0; q < u.splits; ++q) s += p[(int64_t)q * u.ps];
+                g[j] = s;
+            }
+        }
+        // den = F_i G (all l, current values)
+        float den[kSlots];
+#pragma unroll
+        for (int j = 0; j < kSlots; ++j) den[j] = 0.f;
+#pragma unroll
+        for (int jl = 0; jl < kSlots; ++jl) {
+#pragma unroll
+            for (int src = 0; src < kLanesPerRow; ++src) {
+                const int l = src + kLanesPerRow * jl;
+                if (l < r) {
+                    const float fl = __shfl_sync(kFull, f[jl], gbase + src);
+                    const float* Gl = Gs + l * r;
+#pragma unroll
+                    for (int j = 0; j < kSlots; ++j) {
+                        const int k = sub + kLanesPerRow * j;
+                        if (k < r) den[j] = fmaf(fl, Gl[k], den[j]);
+                    }
+                }
+            }
+        }
+        if (kHals) {
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) g[j] -= den[j];
+            // Gauss-Seidel over k = 0..r-1
+#pragma unroll
+            for (int jk = 0; jk < kSlots; ++jk) {
+#pragma unroll
+                for (int src = 0; src < kLanesPerRow; ++src) {
+                    const int k = src + kLanesPerRow * jk;
+                    if (k < r) {
+                        const float gkk = Gs[k * r + k];
+                        float delta = 0.f;
+                        if (sub == src && gkk > 0.f) {
+                            const float nv = fmaxf(0.f, f[jk] + g[jk] / gkk);
+                            delta = nv - f[jk];
+                            f[jk] = nv;
+                        }
+                        delta = __shfl_sync(kFull, delta, gbase + src);
+                        const float* Gk = Gs + k * r;
+#pragma unroll
+                        for (int j = 0; j < kSlots; ++j) {
+                            const int kk = sub + kLanesPerRow * j;
+                            if (kk < r) g[j] = fmaf(-delta, Gk[kk], g[j]);
+                        }
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) f[j] = f[j] * g[j] / fmaxf(den[j], kMuEps);
+        }
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < kSlots; ++j) {
+                const int k = sub + kLanesPerRow * j;
+                if (k < r) u.F[row * u.ldf + k] = f[j];
+            }
+        }
+    }
+}
+
+cudaError_t rows_update_launch(const UpdateArgs& u, int num_sms, bool hals, cudaStream_t st) {
+    if (u.rows <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t rows_per_cta = threads / kLanesPerRow;
+    int64_t grid = ceil_div(u.rows, rows_per_cta);
+    const int64_t cap = 4LL * num_sms;
+    if (grid > cap) grid = cap;
+    const size_t smem = sizeof(float) * u.r * u.r;
+    if (hals)
+        rows_update_kernel<true><<<(unsigned)grid, threads, smem, st>>>(u);
+    else
+        rows_update_kernel<false><<<(unsigned)grid, threads, smem, st>>>(u);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// ANLS: warp-per-row Lawson-Hanson NNLS in FP64.
+// Distributed vectors: entry k lives in lane k & 31, slot k >> 5.
+// ---------------------------------------------------------------------------
+constexpr int kAnlsWarps = 4;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// Solve G_PP z_P = b_P for the passive set `mask` by Cholesky; z = 0 off P.
+// Returns false if a pivot falls below 1e-12 of its original diagonal (the
+// passive columns are numerically dependent).
+__device__ bool solve_passive(const double* G, int r, uint64_t mask, const double b[2], double z[2],
+                              double* L, double* y, int* pidx, int lane) {
+    const int p = __popcll(mask);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int k = lane + 32 * s;
+        if (k < r && ((mask >> k) & 1ull)) {
+            const int pos = __popcll(mask & ((1ull << k) - 1ull));
+            pidx[pos] = k;
+            y[pos] = b[s];
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < p * p; e += 32) {
+        const int i = e / p, j = e - i * p;
+        L[e] = G[pidx[i] * r + pidx[j]];
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int k = 0; k < p; ++k) {
+        const double d0 = L[k * p + k];
+        const double orig = G[pidx[k] * r + pidx[k]];
+        if (!(d0 > 1e-12 * orig)) {
+            ok = false;
+            break;
+        }
+        const double d = sqrt(d0);
+        __syncwarp();
+        if (lane == 0) L[k * p + k] = d;
+        for (int i = k + 1 + lane; i < p; i += 32) L[i * p + k] /= d;
+        __syncwarp();
+        for (int i = k + 1 + lane; i < p; i += 32) {
+            const double lik = L[i * p + k];
+            for (int j = k + 1; j <= i; ++j) L[i * p + j] -= lik * L[j * p + k];
+        }
+        __syncwarp();
+    }
+    if (ok) {
+        // forward substitution L y = b_P
+        for (int j = 0; j < p; ++j) {
+            const double yj = y[j] / L[j * p + j];
+            __syncwarp();
+            if (lane == 0) y[j] = yj;
+            for (int i = j + 1 + lane; i < p; i += 32) y[i] -= L[i * p + j] * yj;
+            __syncwarp();
+        }
+        // back substitution L^T z = y
+        for (int j = p - 1; j >= 0; --j) {
+            const double zj = y[j] / L[j * p + j];
+            __syncwarp();
+            if (lane == 0) y[j] = zj;
+            for (int i = lane; i < j; i += 32) y[i] -= L[j * p + i] * zj;
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int k = lane + 32 * s;
+        z[s] = 0.0;
+        if (ok && k < r && ((mask >> k) & 1ull)) z[s] = y[__popcll(mask & ((1ull << k) - 1ull))];
+    }
+    __syncwarp();
+    return ok;
+}
+
+__global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const UpdateArgs u, int* status) {
+    extern __shared__ double smem[];
+    const int r = u.r;
+    double* G = smem;  // r x r
+    reduce_gram<double>(u, G);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    double* L = G + r * r + (size_t)warp * r * r;
+    double* y = G + r * r + (size_t)kAnlsWarps * r * r + warp * kMaxRank;
+    int* pidx = reinterpret_cast<int*>(G + r * r + (size_t)kAnlsWarps * r * r + kAnlsWarps * kMaxRank) +
+                warp * kMaxRank;
+    const uint64_t all = (r == 64) ? ~0ull : ((1ull << r) - 1ull);
+
+    for (int64_t row = (int64_t)blockIdx.x * kAnlsWarps + warp; row < u.rows;
+         row += (int64_t)gridDim.x * kAnlsWarps) {
+        double b[2], x[2] = {0.0, 0.0}, z[2];
+        uint64_t warm = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int k = lane + 32 * s;
+            b[s] = 0.0;
+            if (k < r) {
+                const float* p = u.P + row * u.ldp + k;
+                double acc = 0.0;
+                for (int q = 0; q < u.splits; ++q) acc += (double)p[(int64_t)q * u.ps];
+                b[s] = acc;
+            }
+            const bool pos = k < r && u.F[row * u.ldf + k] > 0.f;
+            warm |= (uint64_t)__ballot_sync(kFull, pos) << (32 * s);
+        }
+        const double bmax = warp_max(fmax(fabs(b[0]), fabs(b[1])));
+        const double tol = 1e-12 * fmax(1.0, bmax);
+        uint64_t mask = 0, excluded = 0;
+
+        // Warm start from the support of the incoming row: drop the variables
+        // whose unconstrained solution is not positive until the rest is.
+        mask = warm & all;
+        for (int it = 0; it <= r && mask; ++it) {
+            if (!solve_passive(G, r, mask, b, z, L, y, pidx, lane)) {
+                mask = 0;
+                break;
+            }
+            uint64_t badm = 0;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int k = lane + 32 * s;
+                const bool bad = k < r && ((mask >> k) & 1ull) && !(z[s] > 0.0);
+                badm |= (uint64_t)__ballot_sync(kFull, bad) << (32 * s);
+            }
+            if (!badm) {
+                x[0] = z[0];
+                x[1] = z[1];
+                break;
+            }
+            mask &= ~badm;
+        }
+        if (!mask) x[0] = x[1] = 0.0;
+
+        bool capped = false;
+        for (int outer = 0;; ++outer) {
+            // dual w = b - G x
+            double w[2] = {b[0], b[1]};
+            for (int l = 0; l < r; ++l) {
+                const double xl = __shfl_sync(kFull, x[l >> 5], l & 31);
+                if (xl != 0.0) {
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const int k = lane + 32 * s;
+                        if (k < r) w[s] -= G[k * r + l] * xl;
+                    }
+                }
+            }
+            // entering variable: largest positive dual outside P (lowest index on ties)
+            double best = -1.0;
+            int bestk = 1 << 30;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int k = lane + 32 * s;
+                if (k < r && !(((mask | excluded) >> k) & 1ull) && w[s] > tol && w[s] > best) {
+                    best = w[s];
+                    bestk = k;
+                }
+            }
+            const double wbest = warp_max(best);
+            if (!(wbest > tol)) break;
+            const unsigned cand = __ballot_sync(kFull, best == wbest && bestk < (1 << 30));
+            int j = 1 << 30;
+            for (unsigned c = cand; c; c &= c - 1) {
+                const int ln = __ffs(c) - 1;
+                j = min(j, __shfl_sync(kFull, bestk, ln));
+            }
+            j = __shfl_sync(kFull, j, 0);
+            if (outer >= 3 * r) {
+                capped = true;
+                break;
+            }
+            mask |= 1ull << j;
+            for (int it = 0; it <= r; ++it) {
+                if (!solve_passive(G, r, mask, b, z, L, y, pidx, lane)) {
+                    mask &= ~(1ull << j);
+                    excluded |= 1ull << j;
+                    break;
+                }
+                uint64_t badm = 0;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int k = lane + 32 * s;
+                    const bool bad = k < r && ((mask >> k) & 1ull) && !(z[s] > 0.0);
+                    badm |= (uint64_t)__ballot_sync(kFull, bad) << (32 * s);
+                }
+                if (!badm) {
+                    x[0] = z[0];
+                    x[1] = z[1];
+                    break;
+                }
+                // step from x towards z until the first passive variable hits zero
+                double ratio[2] = {INFINITY, INFINITY};
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int k = lane + 32 * s;
+                    if (k < r && ((badm >> k) & 1ull)) ratio[s] = x[s] / (x[s] - z[s]);
+                }
+                const double alpha = warp_min(fmin(ratio[0], ratio[1]));
+                uint64_t drop = 0;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int k = lane + 32 * s;
+                    bool inP = k < r && ((mask >> k) & 1ull);
+                    if (inP) {
+                        x[s] = x[s] + alpha * (z[s] - x[s]);
+                        if (ratio[s] <= alpha) x[s] = 0.0;
+                    }
+                    drop |= (uint64_t)__ballot_sync(kFull, inP && !(x[s] > 0.0)) << (32 * s);
+                }
+                mask &= ~drop;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int k = lane + 32 * s;
+                    if (k >= r || !((mask >> k) & 1ull)) x[s] = 0.0;
+                }
+            }
+        }
+        if (capped && lane == 0) atomicOr(status, 1);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int k = lane + 32 * s;
+            if (k < r) u.F[row * u.ldf + k] = (float)x[s];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t hals_update_launch(const UpdateArgs& a, int num_sms, cudaStream_t st) {
+    return rows_update_launch(a, num_sms, true, st);
+}
+
+cudaError_t mu_update_launch(const UpdateArgs& a, int num_sms, cudaStream_t st) {
+    return rows_update_launch(a, num_sms, false, st);
+}
+
+static size_t anls_smem_bytes(int r) {
+    return sizeof(double) * ((size_t)r * r * (1 + kAnlsWarps) + kAnlsWarps * kMaxRank) +
+           sizeof(int) * kAnlsWarps * kMaxRank;
+}
+
+cudaError_t init_kernel_attributes() {
+    return cudaFuncSetAttribute(anls_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)anls_smem_bytes(kMaxRank));
+}
+
+cudaError_t anls_update_launch(const UpdateArgs& u, int num_sms, int* d_status, cudaStream_t st) {
+    if (u.rows <= 0) return cudaSuccess;
+    const size_t smem = anls_smem_bytes(u.r);
+    int64_t grid = ceil_div(u.rows, kAnlsWarps);
+    const int64_t cap = 8LL * num_sms;
+    if (grid > cap) grid = cap;
+    anls_rows_kernel<<<(unsigned)grid, 32 * kAnlsWarps, smem, st>>>(u, d_status);
+    return cudaGetLastError();
+}
+
+}  // namespace nmfk

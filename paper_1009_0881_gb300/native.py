@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI declared in include/nmf.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Array arguments may be numpy arrays (host memory) or CUDA torch
+tensors (device memory); both must be C-contiguous float32 (float64 for
+outputs that are doubles).  Loading fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NMF_HALS, NMF_MU, NMF_ANLS = 0, 1, 2
+NMF_FP32, NMF_BF16 = 0, 1
+NMF_VCYCLE, NMF_NESTED, NMF_FMG = 0, 1, 2
+ALGOS = {"hals": NMF_HALS, "mu": NMF_MU, "anls": NMF_ANLS}
+CYCLES = {"vcycle": NMF_VCYCLE, "ni": NMF_NESTED, "fmg": NMF_FMG}
+
+STATUS = {0: "NMF_OK", -1: "NMF_EINVAL", -2: "NMF_ENOMEM", -3: "NMF_ENOCONV", -4: "NMF_ECUDA",
+          -5: "NMF_ETIMEOUT", -6: "NMF_EBUSY"}
+
+# (name, restype, argtypes) of every exported entry point of include/nmf.h
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+SIGNATURES = [
+    ("nmf_create", _I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I]),
+    ("nmf_destroy", None, [_P]),
+    ("nmf_last_error", ctypes.c_char_p, [_P]),
+    ("nmf_solve", _I, [_P, _P, _I64, _I64, _I, _I, _I, _I, _I, _I, _P, _P]),
+    ("nmf_solve_ex", _I, [_P, _P, _I64, _I64, _I, _I, _I, _I, _I, _I, _P, _P, _P]),
+    ("nmf_error", _I, [_P, _P, _P, _P, _I64, _I64, _I, ctypes.POINTER(ctypes.c_double)]),
+    ("nmf_schedule", _I64, [_I, _I, _I, ctypes.POINTER(_I64)]),
+    ("nmf_restrict", _I, [_P, _P, _I, _I, _I64, _P]),
+    ("nmf_prolong", _I, [_P, _P, _I, _I, _I64, _P]),
+    ("nmf_products", _I, [_P, _P, _P, _P, _I64, _I64, _I, _P, _P, _P, _P]),
+    ("nmf_sweep", _I, [_P, _P, _I64, _I64, _I, _I, _I, _P, _P]),
+    ("nmf_device_info", _I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_char_p)]),
+    ("nmf_set_stream", _I, [_P, _P]),
+    ("nmf_last_launch_count", _I64, [_P]),
+    ("nmf_profile_sweep", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
+]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("cycle", _I), ("stop_after", _I64), ("trace", ctypes.POINTER(ctypes.c_double)),
+                ("trace_len", _I64), ("trace_count", ctypes.POINTER(_I64))]
+
+
+class NMFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load the shared library (raise if it is absent; never fall back)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(f"GB300 NMF library not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device or host address of a contiguous float array (numpy or torch)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _check_f32(*arrs):
+    for a in arrs:
+        if a is None:
+            continue
+        dt = getattr(a, "dtype", None)
+        if isinstance(a, np.ndarray):
+            if dt != np.float32:
+                raise TypeError("float32 arrays required")
+        elif str(dt) != "torch.float32":
+            raise TypeError("float32 tensors required")
+
+
+class Handle:
+    """An nmf_handle: device workspaces, stream and cached CUDA graphs."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, precision: int = NMF_FP32):
+        self.lib = load()
+        h = _P()
+        rc = self.lib.nmf_create(ctypes.byref(h), device, hbm_budget_bytes, precision)
+        if rc != 0:
+            raise NMFError(rc, "nmf_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nmf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _rc(self, rc: int):
+        if rc != 0:
+            raise NMFError(rc, self.lib.nmf_last_error(self.h).decode())
+        return rc
+
+    # --- entry points -------------------------------------------------------
+    def solve(self, M, grid_h: int, grid_w: int, V, W, algo="hals", levels: int = 1, iters: int = 100,
+              cycle="vcycle", stop_after: int = 0, trace_len: int = 0):
+        """nmf_solve_ex: improves V (m x r) and W (r x n) in place; returns the objective trace if asked."""
+        _check_f32(M, V, W)
+        m, n = M.shape
+        r = V.shape[1]
+        opt = Options()
+        opt.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
+        opt.stop_after = stop_after
+        trace = None
+        count = _I64(0)
+        if trace_len > 0:
+            trace = np.zeros(trace_len, dtype=np.float64)
+            opt.trace = trace.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            opt.trace_len = trace_len
+        opt.trace_count = ctypes.pointer(count)
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        self._rc(self.lib.nmf_solve_ex(self.h, _ptr(M), m, n, grid_h, grid_w, r, a, levels, iters,
+                                       ctypes.byref(opt), _ptr(V), _ptr(W)))
+        if trace is not None:
+            return trace[: min(count.value, trace_len)]
+        return None
+
+    def solve_plain(self, M, grid_h, grid_w, V, W, algo="hals", levels=1, iters=100):
+        """nmf_solve (V-cycle, no options)."""
+        _check_f32(M, V, W)
+        m, n = M.shape
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        return self._rc(self.lib.nmf_solve(self.h, _ptr(M), m, n, grid_h, grid_w, V.shape[1], a, levels, iters,
+                                           _ptr(V), _ptr(W)))
+
+    def sweep(self, M, V, W, algo="hals", sweeps: int = 1):
+        _check_f32(M, V, W)
+        m, n = M.shape
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        self._rc(self.lib.nmf_sweep(self.h, _ptr(M), m, n, V.shape[1], a, sweeps, _ptr(V), _ptr(W)))
+
+    def error(self, M, V, W) -> float:
+        _check_f32(M, V, W)
+        m, n = M.shape
+        out = ctypes.c_double(0.0)
+        self._rc(self.lib.nmf_error(self.h, _ptr(M), _ptr(V), _ptr(W), m, n, V.shape[1], ctypes.byref(out)))
+        return out.value
+
+    def restrict(self, X, grid_h: int, grid_w: int, Y):
+        _check_f32(X, Y)
+        self._rc(self.lib.nmf_restrict(self.h, _ptr(X), grid_h, grid_w, X.shape[1], _ptr(Y)))
+
+    def prolong(self, Y, grid_h: int, grid_w: int, X):
+        _check_f32(X, Y)
+        self._rc(self.lib.nmf_prolong(self.h, _ptr(Y), grid_h, grid_w, Y.shape[1], _ptr(X)))
+
+    def products(self, M, V, W, A=None, B=None, C=None, D=None):
+        _check_f32(M, V, W, A, B, C, D)
+        m, n = M.shape
+        self._rc(self.lib.nmf_products(self.h, _ptr(M), _ptr(V), _ptr(W), m, n, V.shape[1], _ptr(A), _ptr(B),
+                                       _ptr(C), _ptr(D)))
+
+    def device_info(self):
+        sms = _I(0)
+        tag = ctypes.c_char_p()
+        self._rc(self.lib.nmf_device_info(self.h, ctypes.byref(sms), ctypes.byref(tag)))
+        return sms.value, tag.value.decode()
+
+
+    def set_stream(self, stream_ptr: int | None):
+        """nmf_set_stream: run on the given cudaStream_t (an int address), None = own stream."""
+        self._rc(self.lib.nmf_set_stream(self.h, stream_ptr or None))
+
+    def last_launch_count(self) -> int:
+        return int(self.lib.nmf_last_launch_count(self.h))
+
+    def profile_sweep(self, M, V, W, algo="hals", reps: int = 20) -> list[float]:
+        """nmf_profile_sweep: mean ms per launch of [V-step products, V update, W-step products, W update, error]."""
+        _check_f32(M, V, W)
+        m, n = M.shape
+        out = (ctypes.c_float * 5)()
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        self._rc(self.lib.nmf_profile_sweep(self.h, _ptr(M), m, n, V.shape[1], a, _ptr(V), _ptr(W), reps, out))
+        return list(out)
+
+
+def schedule(cycle: str, levels: int, iters: int) -> list[int]:
+    """nmf_schedule: sweeps per level (host-only, no GPU needed)."""
+    lib = load()
+    out = (_I64 * levels)()
+    total = lib.nmf_schedule(CYCLES[cycle], levels, iters, out)
+    if total < 0:
+        raise NMFError(int(total), "nmf_schedule failed")
+    return list(out)

@@ -1,0 +1,51 @@
+"""Write tests/golden/objectives.json: final ||M - VW||_F of the FP64 oracle for the
+seeded workloads (calls only oracle/ and the input generator).
+
+Usage: python tests/golden/make_objectives.py
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+from oracle import nmf_oracle as o  # noqa: E402
+from paper_1009_0881_gb300 import synth  # noqa: E402
+
+CASES = [
+    # name, workload, algo, levels, K, cycle
+    ("grid16_hals_L3_K100", "grid16_n1000_r10", "hals", 3, 100, "vcycle"),
+    ("grid16_hals_L1_K100", "grid16_n1000_r10", "hals", 1, 100, "vcycle"),
+    ("grid19_hals_L3_K500", "grid19_n2429_r49", "hals", 3, 500, "vcycle"),
+    ("grid19_hals_L1_K500", "grid19_n2429_r49", "hals", 1, 500, "vcycle"),
+    ("grid19_mu_L3_K500", "grid19_n2429_r49", "mu", 3, 500, "vcycle"),
+    ("grid19_mu_L1_K500", "grid19_n2429_r49", "mu", 1, 500, "vcycle"),
+    ("grid19_anls_L3_K8", "grid19_n2429_r49", "anls", 3, 8, "vcycle"),
+    ("grid19_hals_fmg_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "fmg"),
+    ("grid19_hals_ni_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "ni"),
+]
+
+
+def main(only=None):
+    path = os.path.join(HERE, "objectives.json")
+    out = json.load(open(path)) if os.path.exists(path) else {}
+    for name, wl, algo, L, K, cyc in CASES:
+        if only and name not in only:
+            continue
+        h, w, n, r, sigma = synth.WORKLOADS[wl]
+        p = synth.make_problem(h, w, n, r, sigma=sigma)
+        t = time.time()
+        V, W = o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc)
+        f = o.objective(p.M.astype(np.float64), V, W)
+        out[name] = {"workload": wl, "algo": algo, "levels": L, "K": K, "cycle": cyc, "objective": f,
+                     "norm_M": float(np.linalg.norm(p.M.astype(np.float64)))}
+        print(f"{name}: {f:.10g} ({time.time() - t:.1f} s)", flush=True)
+        json.dump(out, open(path, "w"), indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or None)

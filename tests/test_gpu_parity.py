@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Tolerances (FP32 path):
+  * transfer operators: a weighted mean of at most 9 float32 values, rtol 2e-6;
+  * products: float32 dot products of length K, norm-wise relative 1e-5;
+  * one sweep from identical iterates: norm-wise relative 1e-5 for V and W
+    (entries clamped at zero make entrywise relative error meaningless);
+  * whole cycles: final objective within 1e-3 relative.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import nmf_oracle as o
+from paper_1009_0881_gb300 import native, synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = json.load(open(os.path.join(ROOT, "tests", "golden", "objectives.json")))
+
+
+@pytest.fixture(scope="module")
+def h():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1009_0881_gb300 import build
+    build.build()
+    with native.Handle(0) as hd:
+        yield hd
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ----------------------------- transfer operators ---------------------------
+
+@pytest.mark.parametrize("gh,gw,cols", [(3, 3, 1), (3, 3, 7), (16, 16, 1000), (19, 19, 49), (10, 7, 5),
+                                        (112, 92, 40), (1, 1, 3), (2, 5, 4), (256, 256, 64)])
+def test_restrict_matches_oracle(h, gh, gw, cols):
+    rng = np.random.default_rng(gh * 100 + gw)
+    X = rng.random((gh * gw, cols)).astype(np.float32)
+    hc, wc = o.coarse_grid(gh, gw)
+    Y = np.zeros((hc * wc, cols), np.float32)
+    h.restrict(X, gh, gw, Y)
+    np.testing.assert_allclose(Y, o.restrict(X, gh, gw), rtol=2e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("gh,gw,cols", [(3, 3, 1), (16, 16, 1000), (19, 19, 49), (10, 7, 5), (112, 92, 40),
+                                        (1, 1, 3), (2, 5, 4), (256, 256, 64)])
+def test_prolong_matches_oracle(h, gh, gw, cols):
+    rng = np.random.default_rng(gh * 7 + gw)
+    hc, wc = o.coarse_grid(gh, gw)
+    Y = rng.random((hc * wc, cols)).astype(np.float32)
+    X = np.zeros((gh * gw, cols), np.float32)
+    h.prolong(Y, gh, gw, X)
+    np.testing.assert_allclose(X, o.prolong(Y, hc, wc, gh, gw), rtol=2e-6, atol=1e-7)
+
+
+def test_transfer_device_pointers(h):
+    import torch
+    X = torch.rand(361, 2429, device="cuda")
+    Y = torch.empty(100, 2429, device="cuda")
+    h.restrict(X, 19, 19, Y)
+    np.testing.assert_allclose(Y.cpu().numpy(), o.restrict(X.cpu().numpy(), 19, 19), rtol=2e-6, atol=1e-7)
+
+
+# ----------------------------- products --------------------------------------
+
+@pytest.mark.parametrize("m,n,r", [(361, 2429, 49), (256, 1000, 10), (100, 37, 64), (25, 2429, 49), (7, 5, 1),
+                                   (1000, 3, 13), (10304, 400, 40), (65, 129, 33)])
+def test_products_match_oracle(h, m, n, r):
+    rng = np.random.default_rng(m + n + r)
+    M = rng.random((m, n)).astype(np.float32)
+    V = rng.random((m, r)).astype(np.float32)
+    W = rng.random((r, n)).astype(np.float32)
+    A = np.zeros((m, r), np.float32)
+    B = np.zeros((r, r), np.float32)
+    C = np.zeros((r, n), np.float32)
+    D = np.zeros((r, r), np.float32)
+    h.products(M, V, W, A, B, C, D)
+    M64, V64, W64 = M.astype(np.float64), V.astype(np.float64), W.astype(np.float64)
+    assert rel(A, M64 @ W64.T) < 1e-5
+    assert rel(B, W64 @ W64.T) < 1e-5
+    assert rel(C, V64.T @ M64) < 1e-5
+    assert rel(D, V64.T @ V64) < 1e-5
+
+
+# ----------------------------- one sweep from identical iterates ------------
+
+SWEEP_CASES = [
+    ("grid19_n2429_r49", None),
+    ("grid16_n1000_r10", None),
+    (None, (8, 8, 37, 1)),      # r = 1, ragged n
+    (None, (9, 7, 130, 64)),    # r = 64, m < r
+    (None, (5, 5, 2429, 49)),   # m = 25 < r = 49 (coarsest level of the 19 x 19 grid)
+]
+
+
+def _problem(case):
+    wl, dims = case
+    if wl:
+        gh, gw, n, r, sigma = synth.WORKLOADS[wl]
+        return synth.make_problem(gh, gw, n, r, sigma=sigma, data_seed=1)
+    gh, gw, n, r = dims
+    return synth.make_problem(gh, gw, n, r, data_seed=5)
+
+
+@pytest.mark.parametrize("algo", ["hals", "mu"])
+@pytest.mark.parametrize("case", SWEEP_CASES)
+def test_single_sweep_matches_oracle(h, algo, case):
+    p = _problem(case)
+    V, W = p.V.copy(), p.W.copy()
+    h.sweep(p.M, V, W, algo, 1)
+    Vo, Wo = o.SWEEPS[algo](p.M.astype(np.float64), p.V.astype(np.float64), p.W.astype(np.float64))
+    assert rel(V, Vo) < 1e-5
+    assert rel(W, Wo) < 1e-5
+    assert (V >= 0).all() and (W >= 0).all()
+
+
+@pytest.mark.parametrize("case", [("grid16_n1000_r10", None), (None, (8, 8, 37, 1)), (None, (9, 7, 130, 12))])
+def test_single_anls_sweep_matches_oracle(h, case):
+    p = _problem(case)
+    V, W = p.V.copy(), p.W.copy()
+    h.sweep(p.M, V, W, "anls", 1)
+    Vo, Wo = o.anls_sweep(p.M.astype(np.float64), p.V.astype(np.float64), p.W.astype(np.float64))
+    assert rel(V, Vo) < 1e-4
+    assert rel(W, Wo) < 1e-4
+
+
+def test_hals_five_sweeps_track_oracle(h):
+    p = _problem(("grid19_n2429_r49", None))
+    V, W = p.V.copy(), p.W.copy()
+    h.sweep(p.M, V, W, "hals", 5)
+    Vo, Wo = o.smooth(p.M.astype(np.float64), p.V.astype(np.float64), p.W.astype(np.float64), "hals", 5)
+    assert rel(V, Vo) < 1e-4 and rel(W, Wo) < 1e-4
+
+
+# ----------------------------- objective --------------------------------------
+
+@pytest.mark.parametrize("m,n,r", [(361, 2429, 49), (256, 1000, 10), (7, 5, 1), (65, 129, 64)])
+def test_error_matches_oracle(h, m, n, r):
+    rng = np.random.default_rng(3 * m + n)
+    M = rng.random((m, n)).astype(np.float32)
+    V = rng.random((m, r)).astype(np.float32) / r
+    W = rng.random((r, n)).astype(np.float32)
+    e = h.error(M, V, W)
+    assert abs(e - o.objective(M, V, W)) <= 1e-6 * o.objective(M, V, W)
+
+
+# ----------------------------- whole cycles -----------------------------------
+
+@pytest.mark.parametrize("name", ["grid16_hals_L3_K100", "grid16_hals_L1_K100", "grid19_hals_L3_K500",
+                                  "grid19_hals_L1_K500", "grid19_mu_L3_K500", "grid19_mu_L1_K500",
+                                  "grid19_anls_L3_K8", "grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100"])
+def test_cycle_final_objective_matches_oracle(h, name):
+    g = GOLDEN[name]
+    gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    V, W = p.V.copy(), p.W.copy()
+    h.solve(p.M, gh, gw, V, W, g["algo"], levels=g["levels"], iters=g["K"], cycle=g["cycle"])
+    f = o.objective(p.M, V, W)
+    assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
+    # the library's own error kernel agrees with the oracle's objective of the same iterate
+    assert abs(h.error(p.M, V, W) - f) <= 1e-6 * f
+
+
+def test_host_and_device_pointers_agree(h):
+    import torch
+    p = _problem(("grid16_n1000_r10", None))
+    V1, W1 = p.V.copy(), p.W.copy()
+    h.solve(p.M, 16, 16, V1, W1, "hals", levels=3, iters=20)
+    Md = torch.from_numpy(p.M).cuda()
+    Vd = torch.from_numpy(p.V.copy()).cuda()
+    Wd = torch.from_numpy(p.W.copy()).cuda()
+    h.solve(Md, 16, 16, Vd, Wd, "hals", levels=3, iters=20)
+    np.testing.assert_array_equal(Vd.cpu().numpy(), V1)
+    np.testing.assert_array_equal(Wd.cpu().numpy(), W1)
+
+
+def test_repeat_solve_is_deterministic(h):
+    p = _problem(("grid19_n2429_r49", None))
+    outs = []
+    for _ in range(2):
+        V, W = p.V.copy(), p.W.copy()
+        h.solve(p.M, 19, 19, V, W, "hals", levels=3, iters=40)
+        outs.append((V, W))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+def test_trace_and_stop_after(h):
+    # the per-sweep trace is the objective of the iterates; stopping early reproduces them exactly
+    p = _problem(("grid16_n1000_r10", None))
+    V, W = p.V.copy(), p.W.copy()
+    tr = h.solve(p.M, 16, 16, V, W, "hals", levels=3, iters=40, trace_len=100)
+    assert len(tr) == native.schedule("vcycle", 3, 40)[0]
+    assert abs(tr[-1] - o.objective(p.M, V, W)) <= 1e-6 * tr[-1]
+    total = sum(native.schedule("vcycle", 3, 40))
+    V2, W2 = p.V.copy(), p.W.copy()
+    h.solve(p.M, 16, 16, V2, W2, "hals", levels=3, iters=40, stop_after=total - 5)
+    V3, W3 = p.V.copy(), p.W.copy()
+    tr3 = h.solve(p.M, 16, 16, V3, W3, "hals", levels=3, iters=40, stop_after=total - 5, trace_len=100)
+    np.testing.assert_array_equal(V2, V3)
+    np.testing.assert_allclose(tr3, tr[: len(tr3)], rtol=0, atol=0)
+    assert abs(tr[len(tr3) - 1] - o.objective(p.M, V2, W2)) <= 1e-6 * tr[-1]
+
+
+def test_mu_objective_nonincreasing_on_gpu(h):
+    p = _problem(("grid19_n2429_r49", None))
+    V, W = p.V.copy(), p.W.copy()
+    tr = h.solve(p.M, 19, 19, V, W, "mu", levels=1, iters=50, trace_len=50)
+    assert np.all(np.diff(tr) <= 1e-6 * tr[:-1])
+
+
+# ----------------------------- errors -----------------------------------------
+
+def test_invalid_inputs_rejected(h):
+    p = _problem(("grid16_n1000_r10", None))
+    bad = p.M.copy()
+    bad[3, 4] = -1.0
+    with pytest.raises(native.NMFError, match="EINVAL"):
+        h.solve(bad, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=2, iters=4)
+    bad[3, 4] = np.nan
+    with pytest.raises(native.NMFError, match="EINVAL"):
+        h.solve(bad, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=2, iters=4)
+    with pytest.raises(native.NMFError, match="EINVAL"):
+        h.solve(p.M, 16, 15, p.V.copy(), p.W.copy(), "hals", levels=2, iters=4)
+    V65 = np.zeros((256, 65), np.float32)
+    with pytest.raises(native.NMFError, match="EINVAL"):
+        h.solve(p.M, 16, 16, V65, np.zeros((65, 1000), np.float32), "hals", levels=2, iters=4)
+    # the handle stays usable after errors
+    V, W = p.V.copy(), p.W.copy()
+    h.solve(p.M, 16, 16, V, W, "hals", levels=2, iters=4)
+
+
+def test_hbm_budget_enforced():
+    p = _problem(("grid16_n1000_r10", None))
+    with native.Handle(0, hbm_budget_bytes=1 << 16) as small:
+        with pytest.raises(native.NMFError, match="ENOMEM"):
+            small.solve(p.M, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=3, iters=4)
