@@ -105,8 +105,8 @@ cudaError_t check_nonneg_launch(const float* X, int64_t ld, int64_t rows, int64_
                                 unsigned long long* d_bad, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
-// ||M - V Wt^T||_F^2 with FP64 accumulation, deterministic: partial sums per
-// CTA into d_partials (size >= error_partials_needed()), final into d_out.
+// ||M - V Wt^T||_F with FP64 accumulation of the squares, deterministic: partial
+// sums per CTA into d_partials (size >= error_partials_needed()), the norm into d_out.
 // ---------------------------------------------------------------------------
 int64_t error_partials_needed(int64_t m, int64_t n);
 cudaError_t error_launch(const float* M, int64_t ldm, const float* V, const float* Wt, int64_t rp,

@@ -695,7 +695,7 @@ int nmf_error(nmf_handle h, const float* M, const float* V, const float* W, int6
     KL(2, error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, m, n, r, p.err_part, p.err_out, h->stream));
     CK(cudaMemcpyAsync(h->h_err, p.err_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    *err_out = sqrt(*h->h_err);
+    *err_out = *h->h_err;
     return NMF_OK;
 }
 

@@ -224,7 +224,7 @@ __global__ void sum_partials_kernel(const double* __restrict__ partials, int64_t
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0];
+    if (threadIdx.x == 0) *out = sqrt(red[0]);
 }
 
 __global__ void sum_splits_kernel(const float* __restrict__ P, int64_t ps, int64_t ldp, int splits,

@@ -24,7 +24,7 @@ CASES = [
     ("grid19_hals_L1_K500", "grid19_n2429_r49", "hals", 1, 500, "vcycle"),
     ("grid19_mu_L3_K500", "grid19_n2429_r49", "mu", 3, 500, "vcycle"),
     ("grid19_mu_L1_K500", "grid19_n2429_r49", "mu", 1, 500, "vcycle"),
-    ("grid19_anls_L3_K8", "grid19_n2429_r49", "anls", 3, 8, "vcycle"),
+    ("grid19_anls_L2_K8", "grid19_n2429_r49", "anls", 2, 8, "vcycle"),
     ("grid19_hals_fmg_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "fmg"),
     ("grid19_hals_ni_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "ni"),
 ]
