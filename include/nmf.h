@@ -65,7 +65,8 @@ typedef enum {
     NMF_ENOCONV = -3,  /* an ANLS active-set solve hit its iteration cap (results are the last iterate) */
     NMF_ECUDA = -4,    /* a CUDA runtime call failed */
     NMF_ETIMEOUT = -5, /* a bounded device-side wait gave up */
-    NMF_EBUSY = -6     /* serving queue full or request not finished */
+    NMF_EBUSY = -6,    /* serving queue full or request not finished */
+    NMF_ETOOBIG = -7   /* problem larger than the fixed scratch of nmf_error_noalloc */
 } nmf_status;
 
 /*
@@ -190,6 +191,38 @@ int64_t nmf_last_launch_count(nmf_handle h);
  */
 int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo,
                       const float* V, const float* W, int reps, float* ms_out);
+
+/*
+ * nmf_error_noalloc - ||M - VW||_F, the same value as nmf_error, computed
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as a
+ * service that reserved all of the GPU's memory up front for its own pool, or
+ * a latency-bound loop that cannot afford the implicit device synchronisation
+ * of cudaMalloc/cudaFree.  It needs no handle and calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ *   M (m x n), V (m x r), W (r x n): device pointers on the calling thread's
+ *     current device, dense row-major float32 (the caller's layout, no copy).
+ *   stream: cudaStream_t (as void*) to run on; NULL = the default stream.
+ *   err_out: host pointer; receives the norm.  The call returns once it is written.
+ *
+ * Scratch: the per-tile partial sums live in one fixed device array of
+ * 65537 doubles (512 KiB + 8 bytes), a file-scope __device__ variable of the
+ * library; every GPU that loads the library holds it until the process
+ * exits.  Its capacity is 65536 tiles of 64 x 64 entries of M, i.e.
+ * ceil(m/64) * ceil(n/64) <= 65536 (for example m = n = 16384); larger
+ * problems are rejected with NMF_ETOOBIG before any work is queued.
+ * The first call on each device looks the array's device address up
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any CUDA stream capture begins.
+ * All calls on a device share the array and each call overwrites what it
+ * uses, so calls whose GPU work overlaps (different streams or threads at
+ * the same time) race and can return wrong values: serialise them.
+ * Returns NMF_OK, NMF_EINVAL (null pointer, m or n < 1, r outside 1..64),
+ * NMF_ETOOBIG, or NMF_ECUDA.
+ */
+int nmf_error_noalloc(const float* M, const float* V, const float* W, int64_t m, int64_t n, int r,
+                      void* stream, double* err_out);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,139 @@
+// nmf_error_noalloc: the Frobenius error ||M - VW||_F without any device
+// allocation, for callers that cannot call cudaMalloc (see include/nmf.h).
+//
+// The per-tile partial sums that nmf_error keeps in its handle's workspace live
+// here in one file-scope device array of fixed size.  Every GPU that loads the
+// library holds that array until the process exits; every call on a device
+// shares it.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "nmf_internal.cuh"
+
+namespace {
+
+constexpr int kTile = 64;                        // 64 x 64 tile of M per CTA
+constexpr int64_t kMaxTiles = 65536;             // scratch capacity: 64 Ki tiles = 512 KiB of doubles
+constexpr int kMaxDevices = 64;
+
+// slots [0, kMaxTiles): one partial sum per tile; slot kMaxTiles: the result
+__device__ __align__(256) double g_error_scratch[kMaxTiles + 1];
+
+std::mutex g_setup_mutex;
+double* g_scratch_addr[kMaxDevices] = {};  // device address of g_error_scratch, per device
+
+// Same arithmetic as the handle-based error kernel, reading the caller's dense
+// layouts directly: M (m x n), V (m x r), W (r x n), all row-major.
+__global__ void __launch_bounds__(256) error_dense_tile_kernel(const float* __restrict__ M,
+                                                               const float* __restrict__ V,
+                                                               const float* __restrict__ W, int64_t m, int64_t n,
+                                                               int r, double* __restrict__ partials) {
+    __shared__ float Vs[nmfk::kMaxRank][kTile + 4];
+    __shared__ float Ws[nmfk::kMaxRank][kTile + 1];
+    const int64_t ntj = (n + kTile - 1) / kTile;
+    const int64_t ti = blockIdx.x / ntj, tj = blockIdx.x - ti * ntj;
+    const int64_t i0 = ti * kTile, j0 = tj * kTile;
+    for (int e = threadIdx.x; e < kTile * r; e += blockDim.x) {
+        const int row = e / r, k = e - row * r;
+        Vs[k][row] = (i0 + row < m) ? V[(i0 + row) * r + k] : 0.f;
+        const int col = e % kTile, kk = e / kTile;
+        Ws[kk][col] = (j0 + col < n) ? W[(int64_t)kk * n + j0 + col] : 0.f;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int k = 0; k < r; ++k) {
+        const float4 v4 = *reinterpret_cast<const float4*>(&Vs[k][ty * 4]);
+        const float va[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(va[a], Ws[k][tx + 16 * b], acc[a][b]);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t i = i0 + ty * 4 + a;
+        if (i >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t j = j0 + tx + 16 * b;
+            if (j >= n) continue;
+            const float e = M[i * n + j] - acc[a][b];
+            s += (double)e * (double)e;
+        }
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+// Sums the `count` partials in a fixed order and writes the norm.
+__global__ void finish_kernel(const double* __restrict__ partials, int64_t count, double* __restrict__ out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int64_t t = threadIdx.x; t < count; t += blockDim.x) s += partials[t];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sqrt(red[0]);
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) and cached.
+cudaError_t scratch_address(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_error_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int nmf_error_noalloc(const float* M, const float* V, const float* W, int64_t m, int64_t n, int r,
+                                 void* stream, double* err_out) {
+    if (!M || !V || !W || !err_out) return NMF_EINVAL;
+    if (m < 1 || n < 1 || r < 1 || r > nmfk::kMaxRank) return NMF_EINVAL;
+    const int64_t tiles = ((m + kTile - 1) / kTile) * ((n + kTile - 1) / kTile);
+    if (tiles > kMaxTiles) return NMF_ETOOBIG;
+    double* scratch = nullptr;
+    if (scratch_address(&scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return NMF_ECUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Every partial slot [0, tiles) is written before it is read and the result
+    // slot is overwritten, so nothing from an earlier call needs clearing.
+    error_dense_tile_kernel<<<(unsigned)tiles, 256, 0, st>>>(M, V, W, m, n, r, scratch);
+    finish_kernel<<<1, 256, 0, st>>>(scratch, tiles, scratch + kMaxTiles);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(err_out, scratch + kMaxTiles, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return NMF_ECUDA;
+    }
+    return NMF_OK;
+}

@@ -21,7 +21,7 @@ ALGOS = {"hals": NMF_HALS, "mu": NMF_MU, "anls": NMF_ANLS}
 CYCLES = {"vcycle": NMF_VCYCLE, "ni": NMF_NESTED, "fmg": NMF_FMG}
 
 STATUS = {0: "NMF_OK", -1: "NMF_EINVAL", -2: "NMF_ENOMEM", -3: "NMF_ENOCONV", -4: "NMF_ECUDA",
-          -5: "NMF_ETIMEOUT", -6: "NMF_EBUSY"}
+          -5: "NMF_ETIMEOUT", -6: "NMF_EBUSY", -7: "NMF_ETOOBIG"}
 
 # (name, restype, argtypes) of every exported entry point of include/nmf.h
 _P = ctypes.c_void_p
@@ -43,6 +43,7 @@ SIGNATURES = [
     ("nmf_set_stream", _I, [_P, _P]),
     ("nmf_last_launch_count", _I64, [_P]),
     ("nmf_profile_sweep", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
+    ("nmf_error_noalloc", _I, [_P, _P, _P, _I64, _I64, _I, _P, ctypes.POINTER(ctypes.c_double)]),
 ]
 
 
@@ -225,6 +226,18 @@ class Handle:
         a = ALGOS[algo] if isinstance(algo, str) else int(algo)
         self._rc(self.lib.nmf_profile_sweep(self.h, _ptr(M), m, n, V.shape[1], a, _ptr(V), _ptr(W), reps, out))
         return list(out)
+
+
+def error_noalloc(M, V, W, stream_ptr: int | None = None) -> float:
+    """nmf_error_noalloc: ||M - VW||_F for device tensors, with no device allocation by the library."""
+    _check_f32(M, V, W)
+    lib = load()
+    m, n = M.shape
+    out = ctypes.c_double(0.0)
+    rc = lib.nmf_error_noalloc(_ptr(M), _ptr(V), _ptr(W), m, n, V.shape[1], stream_ptr or None, ctypes.byref(out))
+    if rc != 0:
+        raise NMFError(rc, "nmf_error_noalloc failed")
+    return out.value
 
 
 def schedule(cycle: str, levels: int, iters: int) -> list[int]:
