@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "fused.cuh"
 #include "nmf_internal.cuh"
 
 using namespace nmfk;
@@ -112,7 +113,9 @@ struct Level {
     float* Mt = nullptr;  // n x ldmt
     int64_t ldmt = 0;
     float* V = nullptr;  // m x rp
-    GemmTask tA{}, tB{}, tC{}, tD{};
+    GemmTask tA{}, tB{}, tC{}, tD{};  // split-K products (nmf_products)
+    HalfSweepLaunch hsV{}, hsW{};     // fused half-sweeps of the solve
+    int gd_count = 0;                 // D partial slabs written by the V-step (64-row tiles of V)
 };
 
 struct Plan {
@@ -125,6 +128,13 @@ struct Plan {
     float* P2 = nullptr;  // C^T partials
     float* PG2 = nullptr; // D partials
     float* tmp = nullptr; // r x n staging for W
+    float* GB = nullptr;  // B = W W^T partial slabs, one per 64-row tile of Wt
+    float* GD = nullptr;  // D = V^T V partial slabs, one per 64-row tile of V
+    float* PA = nullptr;  // reduced A = M W^T rows (ANLS)
+    float* PC = nullptr;  // reduced C^T = M^T V rows (ANLS)
+    int gb_count = 0;
+    int64_t slab = 0;     // floats per Gram slab (r x rp)
+    int* err_flag = nullptr;
     double* err_part = nullptr;
     double* err_out = nullptr;
     double* d_trace = nullptr;
@@ -156,6 +166,7 @@ struct nmf_ctx {
     // pinned host scalars
     unsigned long long* h_bad = nullptr;
     int* h_status = nullptr;
+    int* h_flag = nullptr;
     double* h_err = nullptr;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -262,6 +273,18 @@ void layout(Plan& p, Bump& b, int num_sms) {
     p.P2 = b.take<float>((size_t)max_p2);
     p.PG2 = b.take<float>((size_t)max_pg2);
     p.tmp = b.take<float>((size_t)std::max<int64_t>(std::max<int64_t>(p.r * n, n * rp), p.lv[0].m * rp));
+    p.slab = (int64_t)p.r * rp;
+    p.gb_count = (int)ceil_div(n, 64);
+    int max_gd = 1;
+    for (int l = 0; l < p.L; ++l) {
+        p.lv[l].gd_count = (int)ceil_div(p.lv[l].m, 64);
+        max_gd = std::max(max_gd, p.lv[l].gd_count);
+    }
+    p.GB = b.take<float>((size_t)(p.gb_count * p.slab));
+    p.GD = b.take<float>((size_t)(max_gd * p.slab));
+    p.PA = b.take<float>((size_t)(p.lv[0].m * rp));
+    p.PC = b.take<float>((size_t)(n * rp));
+    p.err_flag = b.take<int>(1);
     p.err_part = b.take<double>((size_t)error_partials_needed(p.lv[0].m, n));
     p.err_out = b.take<double>(1);
     p.d_trace = b.take<double>((size_t)(p.trace_cap > 0 ? p.trace_cap : 1));
@@ -305,6 +328,75 @@ int ensure_workspace(nmf_ctx* h, size_t bytes) {
     return NMF_OK;
 }
 
+// Cluster size for a half-sweep over `tiles` 64-row tiles with product length K:
+// the largest power of two (<= 16) whose clusters all fit on the device at once
+// (one wave; `active[i]` = co-resident clusters of size 2^i) with at least one
+// pipeline stage of K rows per rank.
+int choose_cluster(int tiles, int64_t K, const int* active) {
+    const int ks = half_sweep_stage_rows();
+    int cs = 1;
+    for (int i = 1; i <= 4; ++i) {
+        const int c = 1 << i;
+        if (tiles > active[i] || ceil_div(K, c) < ks) break;
+        cs = c;
+    }
+    return cs;
+}
+
+int plan_half_sweeps(nmf_ctx* h, Plan& p) {
+    int active[5];
+    for (int i = 0; i <= 4; ++i) active[i] = half_sweep_active_clusters(p.br, p.r, 1 << i);
+    const int ks = half_sweep_stage_rows();
+    for (int l = 0; l < p.L; ++l) {
+        Level& v = p.lv[l];
+        // V-step: X = Mt (n x m_l), Y = Wt (n x rp); rows of V
+        HalfSweepLaunch& a = v.hsV;
+        a = HalfSweepLaunch{};
+        a.br = p.br;
+        a.tiles = (int)ceil_div(v.m, 64);
+        a.p.Na = (int)v.m;
+        a.p.K = p.n;
+        a.p.cs = choose_cluster(a.tiles, p.n, active);
+        a.p.kchunk = (int)round_up(ceil_div(p.n, a.p.cs), ks);
+        a.p.r = p.r;
+        a.p.rp = p.rp;
+        a.p.F = v.V;
+        a.p.Gin = p.GB;
+        a.p.gin_count = p.gb_count;
+        a.p.gin_stride = p.slab;
+        a.p.Gout = p.GD;
+        a.p.gout_stride = p.slab;
+        a.p.Pout = p.PA;
+        a.p.err_flag = p.err_flag;
+        cudaError_t e = make_tmap_f32(&a.tmX, v.Mt, v.m, p.n, v.ldmt, 64, ks);
+        if (e == cudaSuccess) e = make_tmap_f32(&a.tmY, p.Wt, p.rp, p.n, p.rp, p.br, ks);
+        if (e != cudaSuccess) return fail(h, NMF_ECUDA, "TMA descriptor (V-step) failed: %s", cudaGetErrorString(e));
+        // W-step: X = M (m_l x n), Y = V (m_l x rp); rows of Wt
+        HalfSweepLaunch& b = v.hsW;
+        b = HalfSweepLaunch{};
+        b.br = p.br;
+        b.tiles = p.gb_count;
+        b.p.Na = (int)p.n;
+        b.p.K = v.m;
+        b.p.cs = choose_cluster(b.tiles, v.m, active);
+        b.p.kchunk = (int)round_up(ceil_div(v.m, b.p.cs), ks);
+        b.p.r = p.r;
+        b.p.rp = p.rp;
+        b.p.F = p.Wt;
+        b.p.Gin = p.GD;
+        b.p.gin_count = v.gd_count;
+        b.p.gin_stride = p.slab;
+        b.p.Gout = p.GB;
+        b.p.gout_stride = p.slab;
+        b.p.Pout = p.PC;
+        b.p.err_flag = p.err_flag;
+        e = make_tmap_f32(&b.tmX, v.M, p.n, v.m, p.ldm, 64, ks);
+        if (e == cudaSuccess) e = make_tmap_f32(&b.tmY, v.V, p.rp, v.m, p.rp, p.br, ks);
+        if (e != cudaSuccess) return fail(h, NMF_ECUDA, "TMA descriptor (W-step) failed: %s", cudaGetErrorString(e));
+    }
+    return NMF_OK;
+}
+
 int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap) {
     p.m = m;
     p.n = n;
@@ -332,70 +424,66 @@ int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, 
     real.base = h->ws;
     real.cap = h->ws_cap;
     layout(p, real, h->num_sms);
-    return NMF_OK;
+    return plan_half_sweeps(h, p);
 }
 
-UpdateArgs v_update_args(const Plan& p, const Level& v) {
-    UpdateArgs u{};
-    u.F = v.V;
-    u.ldf = p.rp;
-    u.P = p.P1;
-    u.ps = v.tA.split_stride;
-    u.ldp = p.rp;
-    u.splits = v.tA.splits;
-    u.PG = p.PG1;
-    u.pgs = v.tB.split_stride;
-    u.ldpg = p.rp;
-    u.gsplits = v.tB.splits;
-    u.rows = v.m;
-    u.r = p.r;
-    return u;
-}
-
-UpdateArgs w_update_args(const Plan& p, const Level& v) {
-    UpdateArgs u{};
-    u.F = p.Wt;
-    u.ldf = p.rp;
-    u.P = p.P2;
-    u.ps = v.tC.split_stride;
-    u.ldp = p.rp;
-    u.splits = v.tC.splits;
-    u.PG = p.PG2;
-    u.pgs = v.tD.split_stride;
-    u.ldpg = p.rp;
-    u.gsplits = v.tD.splits;
-    u.rows = p.n;
-    u.r = p.r;
-    return u;
-}
-
-cudaError_t run_update(nmf_ctx* h, const Plan& p, const UpdateArgs& u, nmf_algo algo) {
-    switch (algo) {
-        case NMF_HALS: return hals_update_launch(u, h->num_sms, h->stream);
-        case NMF_MU: return mu_update_launch(u, h->num_sms, h->stream);
-        default: return anls_update_launch(u, h->num_sms, p.d_status, h->stream);
-    }
-}
-
-// One sweep of the inner algorithm at level l: products for the V-step, V-step,
-// products for the W-step (with the new V), W-step.
-cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo) {
+// One sweep of the inner algorithm at level l: the V-step (products M W^T and
+// the reduction of the B = W W^T slabs, then the new rows of V and their D
+// slabs) and the W-step (products M^T V, reduction of the D slabs, new rows of
+// Wt and their B slabs).  HALS and MU update inside the fused kernel; ANLS
+// stores the reduced products and runs the active-set solver on them.
+cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64_t* launches) {
     const Level& v = p.lv[l];
-    GemmBatch b1{};
-    b1.t[0] = v.tA;
-    b1.t[1] = v.tB;
-    b1.ntasks = 2;
-    cudaError_t e = gemm_tn_launch(b1, p.br, h->stream);
+    const int mode = algo == NMF_HALS ? kModeHals : (algo == NMF_MU ? kModeMu : kModeStore);
+    HalfSweepLaunch a = v.hsV;
+    a.mode = mode;
+    cudaError_t e = half_sweep_launch(a, h->stream);
     if (e != cudaSuccess) return e;
-    e = run_update(h, p, v_update_args(p, v), algo);
+    ++*launches;
+    if (algo == NMF_ANLS) {
+        UpdateArgs u{};
+        u.F = v.V;
+        u.ldf = p.rp;
+        u.P = p.PA;
+        u.ps = 0;
+        u.ldp = p.rp;
+        u.splits = 1;
+        u.PG = p.GB;
+        u.pgs = p.slab;
+        u.ldpg = p.rp;
+        u.gsplits = p.gb_count;
+        u.rows = v.m;
+        u.r = p.r;
+        e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
+        if (e == cudaSuccess) e = gram_tiles_launch(v.V, v.m, p.r, p.rp, p.GD, p.slab, h->stream);
+        if (e != cudaSuccess) return e;
+        *launches += 2;
+    }
+    HalfSweepLaunch b = v.hsW;
+    b.mode = mode;
+    e = half_sweep_launch(b, h->stream);
     if (e != cudaSuccess) return e;
-    GemmBatch b2{};
-    b2.t[0] = v.tC;
-    b2.t[1] = v.tD;
-    b2.ntasks = 2;
-    e = gemm_tn_launch(b2, p.br, h->stream);
-    if (e != cudaSuccess) return e;
-    return run_update(h, p, w_update_args(p, v), algo);
+    ++*launches;
+    if (algo == NMF_ANLS) {
+        UpdateArgs u{};
+        u.F = p.Wt;
+        u.ldf = p.rp;
+        u.P = p.PC;
+        u.ps = 0;
+        u.ldp = p.rp;
+        u.splits = 1;
+        u.PG = p.GD;
+        u.pgs = p.slab;
+        u.ldpg = p.rp;
+        u.gsplits = v.gd_count;
+        u.rows = p.n;
+        u.r = p.r;
+        e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
+        if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.GB, p.slab, h->stream);
+        if (e != cudaSuccess) return e;
+        *launches += 2;
+    }
+    return cudaSuccess;
 }
 
 // Restrictions of M for every level (computed once per solve, footnote of
@@ -414,8 +502,10 @@ cudaError_t enqueue_hierarchy(nmf_ctx* h, const Plan& p) {
 
 cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& ops, nmf_algo algo,
                              int64_t stop_after, bool trace, int64_t* fine_sweeps) {
-    int64_t done = 0, tidx = 0;
-    cudaError_t e = cudaSuccess;
+    int64_t done = 0, tidx = 0, launches = 0;
+    // B = W W^T slabs of the initial W, consumed by the first V-step
+    cudaError_t e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.GB, p.slab, h->stream);
+    if (e != cudaSuccess) return e;
     for (const Op& op : ops) {
         const Level& f = p.lv[op.level];
         if (op.kind == OP_RESTRICT_V) {
@@ -427,7 +517,7 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
         } else {
             for (int64_t s = 0; s < op.count; ++s) {
                 if (stop_after > 0 && done >= stop_after) break;
-                e = enqueue_sweep(h, p, op.level, algo);
+                e = enqueue_sweep(h, p, op.level, algo, &launches);
                 if (e != cudaSuccess) return e;
                 ++done;
                 if (op.level == 0) {
@@ -531,6 +621,7 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     rc = stage_problem(h, p, M, V, W);
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
     CK(cudaMemcpyAsync(h->h_bad, p.d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
 
     // the whole hierarchy + schedule as one cached CUDA graph
@@ -572,8 +663,10 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     h->launches += ge.kernels;
     CK(cudaGraphLaunch(exec, h->stream));
     CK(cudaMemcpyAsync(h->h_status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->h_flag, p.err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (*h->h_bad) return fail(h, NMF_EINVAL, "%llu negative, NaN or infinite entries in M, V0 or W0", *h->h_bad);
+    if (*h->h_flag) return fail(h, NMF_ETIMEOUT, "a bounded wait for an asynchronous copy gave up");
 
     // results back to the caller's layout
     const Level& f = p.lv[0];
@@ -615,13 +708,14 @@ int nmf_create(nmf_handle* out, int device, size_t hbm_budget_bytes, nmf_precisi
         cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(&h->h_bad, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess ||
-        cudaMallocHost(&h->h_err, sizeof(double)) != cudaSuccess) {
+        cudaMallocHost(&h->h_err, sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->h_flag, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         nmf_destroy(h);
         return NMF_ECUDA;
     }
     h->stream = h->own_stream;
-    if (init_kernel_attributes() != cudaSuccess) {
+    if (init_kernel_attributes() != cudaSuccess || tma_init() != cudaSuccess || half_sweep_init() != cudaSuccess) {
         cudaGetLastError();
         nmf_destroy(h);
         return NMF_ECUDA;
@@ -638,6 +732,7 @@ void nmf_destroy(nmf_handle h) {
     if (h->h_bad) cudaFreeHost(h->h_bad);
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
@@ -809,7 +904,10 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
     rc = stage_problem(h, p, M, V, W);
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
+    KL(1, gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.GB, p.slab, h->stream));
     const Level& v = p.lv[0];
+    const int mode = algo == NMF_HALS ? kModeHals : (algo == NMF_MU ? kModeMu : kModeStore);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -819,24 +917,42 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
         for (int it = -1; it < reps; ++it) {
             if (it == 0) cudaEventRecord(e0, h->stream);
             cudaError_t e = cudaSuccess;
+            int nl = 1;
             if (phase == 0 || phase == 2) {
-                GemmBatch b{};
-                b.t[0] = phase == 0 ? v.tA : v.tC;
-                b.t[1] = phase == 0 ? v.tB : v.tD;
-                b.ntasks = 2;
-                e = gemm_tn_launch(b, p.br, h->stream);
-            } else if (phase == 1) {
-                e = run_update(h, p, v_update_args(p, v), algo);
-            } else if (phase == 3) {
-                e = run_update(h, p, w_update_args(p, v), algo);
+                HalfSweepLaunch hl = phase == 0 ? v.hsV : v.hsW;
+                hl.mode = mode;
+                e = half_sweep_launch(hl, h->stream);
+            } else if (phase == 1 || phase == 3) {
+                if (algo != NMF_ANLS) {
+                    nl = 0;
+                } else {
+                    const bool vstep = phase == 1;
+                    UpdateArgs u{};
+                    u.F = vstep ? v.V : p.Wt;
+                    u.ldf = p.rp;
+                    u.P = vstep ? p.PA : p.PC;
+                    u.ldp = p.rp;
+                    u.splits = 1;
+                    u.PG = vstep ? p.GB : p.GD;
+                    u.pgs = p.slab;
+                    u.ldpg = p.rp;
+                    u.gsplits = vstep ? p.gb_count : v.gd_count;
+                    u.rows = vstep ? v.m : p.n;
+                    u.r = p.r;
+                    e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
+                    if (e == cudaSuccess)
+                        e = gram_tiles_launch(u.F, u.rows, p.r, p.rp, vstep ? p.GD : p.GB, p.slab, h->stream);
+                    nl = 2;
+                }
             } else {
                 e = error_launch(v.M, p.ldm, v.V, p.Wt, p.rp, m, n, r, p.err_part, p.err_out, h->stream);
+                nl = 2;
             }
             if (e != cudaSuccess) {
                 out_rc = fail(h, NMF_ECUDA, "profile launch failed: %s", cudaGetErrorString(e));
                 break;
             }
-            h->launches += (phase == 4) ? 2 : 1;
+            h->launches += nl;
         }
         if (out_rc != NMF_OK) break;
         cudaEventRecord(e1, h->stream);

@@ -25,8 +25,12 @@ CASES = [
     ("grid19_mu_L3_K500", "grid19_n2429_r49", "mu", 3, 500, "vcycle"),
     ("grid19_mu_L1_K500", "grid19_n2429_r49", "mu", 1, 500, "vcycle"),
     ("grid19_anls_L2_K8", "grid19_n2429_r49", "anls", 2, 8, "vcycle"),
-    ("grid19_hals_fmg_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "fmg"),
-    ("grid19_hals_ni_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "ni"),
+    # full multigrid and nested iteration start on the coarsest level: keep m_l >= r there
+    ("grid19_hals_fmg_L2_K100", "grid19_n2429_r49", "hals", 2, 100, "fmg"),
+    ("grid19_hals_ni_L2_K100", "grid19_n2429_r49", "hals", 2, 100, "ni"),
+    ("grid16_hals_fmg_L3_K100", "grid16_n1000_r10", "hals", 3, 100, "fmg"),
+    ("grid16_hals_ni_L3_K100", "grid16_n1000_r10", "hals", 3, 100, "ni"),
+    ("grid16_mu_fmg_L3_K100", "grid16_n1000_r10", "mu", 3, 100, "fmg"),
 ]
 
 

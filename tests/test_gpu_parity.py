@@ -175,7 +175,8 @@ def test_error_matches_oracle(h, m, n, r):
 
 @pytest.mark.parametrize("name", ["grid16_hals_L3_K100", "grid16_hals_L1_K100", "grid19_hals_L3_K500",
                                   "grid19_hals_L1_K500", "grid19_mu_L3_K500", "grid19_mu_L1_K500",
-                                  "grid19_anls_L2_K8", "grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100"])
+                                  "grid19_anls_L2_K8", "grid19_hals_fmg_L2_K100", "grid19_hals_ni_L2_K100",
+                                  "grid16_hals_fmg_L3_K100", "grid16_hals_ni_L3_K100", "grid16_mu_fmg_L3_K100"])
 def test_cycle_final_objective_matches_oracle(h, name):
     g = GOLDEN[name]
     gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
