@@ -49,6 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--levels", type=int, default=3)
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-form", action="store_true")
     ap.add_argument("--_oracle_sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -386,63 +387,134 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
         out["plain_fp32_single_level"] = plain
 
     out["roofline"], out["kernel_times_per_step_ms"] = roofline(args, h, Md, gh, gw, n, r, sched)
+    if not args.no_precision_form:
+        out["precision_form"] = precision_form(args)
     return out
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
 
 
 def roofline(args, h, Md, gh, gw, n, r, sched):
     """Per-kernel CUDA-event timing at each level's size, weighted by the sweep schedule.
 
-    Algorithmic flops per launch (Appendix A.1 accounting, multiply-add = 2):
-      V-step products  A = M W^T, B = W W^T : 2 m_l n r + 2 n r^2
-      W-step products  C = V^T M, D = V^T V : 2 m_l n r + 2 m_l r^2
-      V update 2 m_l r^2,  W update 2 n r^2  (the V(WW^T) / (V^T V)W products)
+    The FP32 path runs one fused kernel per half-sweep (products, reduction and
+    factor update).  Algorithmic flops per launch (Appendix A.1 accounting,
+    multiply-add = 2):
+      V-step  A = M W^T (2 m_l n r) + V(W W^T) (2 m_l r^2)
+      W-step  C = V^T M (2 m_l n r) + (V^T V) W (2 n r^2)
+    The Gram matrices W W^T and V^T V (2 n r^2, 2 m_l r^2) are also formed, from
+    the updated rows, but are counted once with the update term as in Appendix A.1.
     """
     import torch
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
+    peaks = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sms, _ = h.device_info()
     fp32_peak = n_sms * 128 * 2 * sm_mhz * 1e6  # FFMA lanes x 2 flops x clock
     dev = Md.device
     Ml = Md
     hh, ww = gh, gw
-    kinds = {"products (gemm_tn_kernel)": [0.0, 0.0, 0], "update (rows_update_kernel)": [0.0, 0.0, 0],
-             "error (error_tile_kernel)": [0.0, 0.0, 0]}
+    hs = "half_sweep_kernel (fused products + update)"
+    kinds = {hs: [0.0, 0.0, 0], "error_tile_kernel": [0.0, 0.0, 0]}
     g = torch.Generator(device="cpu").manual_seed(0)
     W = torch.rand(r, n, generator=g).to(dev)
     for lvl, count in enumerate(sched):
         ml = hh * ww
         V = torch.rand(ml, r, generator=g).to(dev)
         t = h.profile_sweep(Ml, V, W, args.algo, reps=50)
-        fl = [2 * ml * n * r + 2 * n * r * r, 2 * ml * r * r, 2 * ml * n * r + 2 * ml * r * r, 2 * n * r * r,
-              2 * ml * n * r]
-        for ph, kind in ((0, "products (gemm_tn_kernel)"), (2, "products (gemm_tn_kernel)"),
-                         (1, "update (rows_update_kernel)"), (3, "update (rows_update_kernel)")):
-            kinds[kind][0] += count * t[ph]
-            kinds[kind][1] += count * fl[ph]
-            kinds[kind][2] += count
+        flv = 2 * ml * n * r + 2 * ml * r * r
+        flw = 2 * ml * n * r + 2 * n * r * r
+        kinds[hs][0] += count * (t[0] + t[2])
+        kinds[hs][1] += count * (flv + flw)
+        kinds[hs][2] += 2 * count
         if lvl == 0:
-            kinds["error (error_tile_kernel)"] = [t[4], fl[4], 1]
+            kinds["error_tile_kernel"] = [t[4], 2 * ml * n * r, 1]
         if lvl + 1 < len(sched):
             hc, wc = (hh + 1) // 2, (ww + 1) // 2
             Mc = torch.empty(hc * wc, n, device=dev)
             h.restrict(Ml, hh, ww, Mc)
             Ml, hh, ww = Mc, hc, wc
     times = {k: v[0] for k, v in kinds.items()}
-    dom = max(times, key=times.get)
-    ms, flops, launches = kinds[dom]
+    ms, flops, launches = kinds[hs]
     achieved = flops / (ms / 1e3) / 1e12
     peak = fp32_peak / 1e12
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roof = {"kernel": hs, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None, "launches_per_step": launches,
             "mean_launch_us": 1e3 * ms / launches,
             "peak_basis": f"FP32 FFMA: {n_sms} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (derived)"}
     return roof, times
 
+
+PRECISION_WORKLOADS = [("grid112x92_n400_r40", 3, 100), ("grid256_n2000_r64", 3, 20)]
+
+
+def precision_form(args, reps=3):
+    """BF16 operands on the tensor cores (tcgen05, FP32 accumulation) next to the plain FP32
+    path on the precision-form workloads; objective against the FP64 oracle's (stored) value."""
+    import torch
+
+    from paper_1009_0881_gb300 import native, synth
+
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "objectives.json")))
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    stream = torch.cuda.current_stream()
+    out = {}
+    for wl, L, K in PRECISION_WORKLOADS:
+        gh, gw, n, r, sigma = synth.WORKLOADS[wl]
+        p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+        m = gh * gw
+        Md = torch.from_numpy(p.M).cuda()
+        V0 = torch.from_numpy(p.V).cuda()
+        W0 = torch.from_numpy(p.W).cuda()
+        sweeps = sum(native.schedule("vcycle", L, K))
+        key = f"{wl.split('_')[0]}_hals_L{L}_K{K}"
+        fstar = golden.get(key, {}).get("objective")
+        res = {"levels": L, "iters": K, "sweeps": sweeps, "m": m, "n": n, "r": r}
+        for label, prec in (("bf16_tcgen05", native.NMF_BF16), ("fp32", native.NMF_FP32)):
+            with native.Handle(0, precision=prec) as hh:
+                hh.set_stream(stream.cuda_stream)
+                V = V0.clone()
+                W = W0.clone()
+                ms = []
+                for it in range(1 + reps):
+                    V.copy_(V0)
+                    W.copy_(W0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    hh.solve(Md, gh, gw, V, W, "hals", levels=L, iters=K)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if it:
+                        ms.append(e0.elapsed_time(e1))
+                f = hh.error(Md, V, W)
+                t = statistics.median(ms)
+                entry = {"ms_per_solve": t, "sweeps_per_s": sweeps / (t / 1e3), "objective": f,
+                         "rel_diff_vs_fp64_oracle": None if fstar is None else (f - fstar) / fstar}
+                if prec == native.NMF_BF16:
+                    # tcgen05 product of the V-step at the finest level: HBM roofline
+                    g = torch.Generator(device="cpu").manual_seed(1)
+                    Vr = torch.rand(m, r, generator=g).cuda()
+                    tt = hh.profile_sweep(Md, Vr, W0, "hals", reps=20)
+                    # algorithmic bytes: read bf16 M and W once, write the FP32 product once
+                    bytes_v = m * n * 2 + r * n * 2 + m * r * 4
+                    ach = bytes_v / (tt[0] / 1e3) / 1e9
+                    entry["kernel_ms"] = {"tc_gemm V-step": tt[0], "gram+rows V": tt[1], "tc_gemm W-step": tt[2],
+                                          "gram+rows W": tt[3]}
+                    entry["roofline"] = {"kernel": "tc_gemm_kernel (V-step, A = M W^T, finest level)",
+                                         "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                         "frac": ach / hbm, "traffic": None,
+                                         "algorithmic_bytes": bytes_v}
+                res[label] = entry
+        res["oracle_fp64_objective"] = fstar
+        out[wl] = res
+    return out
 
 
 if __name__ == "__main__":

@@ -1,0 +1,213 @@
+// Kernels around the tcgen05 products of the BF16 precision form: BF16 operand
+// copies, the final Gram matrix from per-tile slabs, and the row update.
+//
+// The row update reads the split-K partial tiles of the product (summed in a
+// fixed order), runs the HALS or MU step of Algorithm HALS / MU on 64 rows per
+// CTA with the same code as the fused FP32 kernel (rowupdate.cuh), stores the
+// new rows in FP32, their transposed BF16 copy (the next product's operand)
+// and the Gram slab F_tile^T F_tile of the tile for the other half-sweep.
+#include <cuda_bf16.h>
+
+#include "fused.cuh"
+#include "ptx.cuh"
+#include "rowupdate.cuh"
+#include "tc_gemm.cuh"
+
+namespace nmfk {
+
+namespace {
+
+using rowupd::f4add;
+using rowupd::update_rows;
+constexpr int NT = rowupd::NT;
+constexpr int BA = 64;
+
+__global__ void to_bf16_kernel(const float* __restrict__ in, int64_t ldi, int64_t rows, int64_t cols,
+                               __nv_bfloat16* __restrict__ out, int64_t ldo) {
+    const int64_t total = rows * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / cols, c = t - r * cols;
+        out[r * ldo + c] = __float2bfloat16_rn(in[r * ldi + c]);
+    }
+}
+
+// 32 x 32 tiles through shared memory
+__global__ void to_bf16_t_kernel(const float* __restrict__ in, int64_t ldi, int64_t rows, int64_t cols,
+                                 __nv_bfloat16* __restrict__ out, int64_t ldo) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t r = r0 + dy, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[dy][threadIdx.x] = in[r * ldi + c];
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t c = c0 + dy, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[c * ldo + r] = __float2bfloat16_rn(tile[threadIdx.x][dy]);
+    }
+}
+
+__global__ void gram_final_kernel(const float* __restrict__ slabs, int count, int64_t stride, int n, float* __restrict__ G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float s = 0.f;
+    for (int q = 0; q < count; ++q) s += slabs[(int64_t)q * stride + e];
+    G[e] = s;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) {
+    extern __shared__ __align__(16) float sm[];
+    const int r = q.r, rp = q.rp;
+    float* Gs = sm;                       // r x rp
+    float* Ginv = Gs + r * rp;            // kMaxRank
+    float* Fn = Ginv + kMaxRank;          // BA x kMaxRank
+    float* Ared = Fn + BA * kMaxRank;     // BA x kMaxRank
+    float* Dn = Ared + BA * kMaxRank;     // BA x kMaxRank
+    float* Fg = Dn + BA * kMaxRank;       // r x rp
+    const int tid = threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * BA;
+    const int R = BA;
+    const int Q4 = rp / 4;
+
+    // incoming rows (async), Gram matrix, reduced product rows
+    for (int e = tid; e < BA * (kMaxRank / 4); e += NT) {
+        const int rr = e / (kMaxRank / 4), k4 = e - rr * (kMaxRank / 4);
+        const int64_t row = row0 + rr;
+        float* dst = Fn + rr * kMaxRank + 4 * k4;
+        if (k4 < Q4)
+            ptx::cp_async16(dst, q.F + (row < q.rows ? row : 0) * rp + 4 * k4, row < q.rows ? 16u : 0u);
+        else
+            *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    ptx::cp_async_commit();
+    if (MODE != rowupd::kModeStore) {
+        for (int e = tid; e < r * Q4; e += NT)
+            reinterpret_cast<float4*>(Gs)[e] = reinterpret_cast<const float4*>(q.G)[e];
+        for (int e = tid; e < BA * Q4; e += NT) {
+            const int rr = e / Q4, k4 = e - rr * Q4;
+            const int64_t row = row0 + rr;
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < q.rows) {
+                const float4* src = reinterpret_cast<const float4*>(q.P + row * rp) + k4;
+                const int64_t ps4 = q.ps / 4;
+#pragma unroll 4
+                for (int sp = 0; sp < q.splits; ++sp) s = f4add(s, src[sp * ps4]);
+            }
+            *reinterpret_cast<float4*>(Ared + rr * kMaxRank + 4 * k4) = s;
+        }
+    }
+    ptx::cp_async_wait_all();
+    __syncthreads();
+
+    if (MODE != rowupd::kModeStore) {
+        for (int k = tid; k < kMaxRank; k += NT) Ginv[k] = (k < r && Gs[k * rp + k] > 0.f) ? 1.f / Gs[k * rp + k] : 0.f;
+        for (int e = tid; e < R * kMaxRank; e += NT) {
+            const int rr = e / kMaxRank, k = e - rr * kMaxRank;
+            float s = 0.f;
+            if (k < r) {
+                const float* fr = Fn + rr * kMaxRank;
+                for (int l = 0; l < r; ++l) s = fmaf(fr[l], Gs[l * rp + k], s);
+            }
+            Dn[e] = s;
+        }
+        __syncthreads();
+        update_rows<8, MODE>(q.F, (int)q.rows, r, rp, R, row0, Fn, Ared, Dn, Gs, Ginv);
+        __syncthreads();
+    } else {
+        // rows past the end read as zero already; nothing to update
+        __syncthreads();
+    }
+
+    // transposed BF16 copy of the new rows: Fb[k][row]
+    if (q.Fb) {
+        for (int e = tid; e < r * BA; e += NT) {
+            const int k = e / BA, rr = e - k * BA;
+            const int64_t row = row0 + rr;
+            if (row < q.rows) q.Fb[(int64_t)k * q.ldb + row] = __float2bfloat16_rn(Fn[rr * kMaxRank + k]);
+        }
+    }
+    // Gram slab of the tile, 4 x 4 outputs per thread
+    {
+        const int tx = tid & 15, ty = tid >> 4;
+        float ga[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ga[i][j] = 0.f;
+        for (int rr = 0; rr < R; ++rr) {
+            const float4 u = *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + ty * 4);
+            const float4 v = *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + tx * 4);
+            const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ga[i][j] = fmaf(uu[i], vv[j], ga[i][j]);
+        }
+        float* gout = q.Gout + (int64_t)blockIdx.x * q.gout_stride;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int l = ty * 4 + i;
+            if (l < r && tx * 4 < rp)
+                *reinterpret_cast<float4*>(gout + l * rp + tx * 4) = make_float4(ga[i][0], ga[i][1], ga[i][2], ga[i][3]);
+        }
+    }
+}
+
+size_t rows_smem_bytes(int r, int rp) {
+    return sizeof(float) * ((size_t)2 * r * rp + kMaxRank + 3 * BA * kMaxRank);
+}
+
+}  // namespace
+
+cudaError_t make_tmap_bf16_sw128(CUtensorMap* map, const __nv_bfloat16* base, uint64_t width, uint64_t height,
+                                 uint64_t ld, uint32_t box_h) {
+    return make_tmap_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, width, height, ld * 2, 64, box_h,
+                        CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+cudaError_t to_bf16_launch(const float* in, int64_t ldi, int64_t rows, int64_t cols, __nv_bfloat16* out, int64_t ldo,
+                           bool transpose, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (transpose) {
+        dim3 block(32, 8), grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
+        to_bf16_t_kernel<<<grid, block, 0, st>>>(in, ldi, rows, cols, out, ldo);
+    } else {
+        int64_t g = ceil_div(rows * cols, 256);
+        if (g > 65535LL * 16) g = 65535LL * 16;
+        to_bf16_kernel<<<(unsigned)g, 256, 0, st>>>(in, ldi, rows, cols, out, ldo);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int r, int rp, float* G, cudaStream_t st) {
+    const int n = r * rp;
+    gram_final_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(slabs, count, stride, n, G);
+    return cudaGetLastError();
+}
+
+cudaError_t rows_update_init() {
+    const int maxs = (int)rows_smem_bytes(kMaxRank, kMaxRank);
+    cudaError_t e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeHals>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeMu>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 maxs);
+    return e;
+}
+
+cudaError_t rows_update_launch(const RowsParams& q, int mode, cudaStream_t st) {
+    if (q.rows <= 0) return cudaSuccess;
+    const size_t smem = rows_smem_bytes(q.r, q.rp);
+    const unsigned grid = (unsigned)ceil_div(q.rows, BA);
+    switch (mode) {
+        case rowupd::kModeHals: rows_update_kernel<rowupd::kModeHals><<<grid, NT, smem, st>>>(q); break;
+        case rowupd::kModeMu: rows_update_kernel<rowupd::kModeMu><<<grid, NT, smem, st>>>(q); break;
+        default: rows_update_kernel<rowupd::kModeStore><<<grid, NT, smem, st>>>(q); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nmfk

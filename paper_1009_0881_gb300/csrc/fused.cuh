@@ -36,6 +36,10 @@ struct HalfSweepLaunch {
 };
 
 cudaError_t tma_init();
+// 2-D tiled tensor map (row-major height x width, ld_bytes between rows).
+cudaError_t make_tmap_2d(CUtensorMap* map, CUtensorMapDataType type, const void* base, uint64_t width,
+                         uint64_t height, uint64_t ld_bytes, uint32_t box_w, uint32_t box_h,
+                         CUtensorMapSwizzle swizzle);
 cudaError_t make_tmap_f32(CUtensorMap* map, const float* base, uint64_t width, uint64_t height, uint64_t ld,
                           uint32_t box_w, uint32_t box_h);
 cudaError_t half_sweep_init();

@@ -1,0 +1,152 @@
+// Row updates shared by the fused half-sweep kernel and the standalone update
+// kernel of the BF16 path: the HALS Gauss-Seidel step (Algorithm HALS) and the
+// MU step (Algorithm MU) on rows of a tall factor, plus two small helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "nmf_internal.cuh"
+
+namespace nmfk {
+namespace rowupd {
+
+constexpr int NT = 256;  // threads per CTA of the kernels that use these helpers
+constexpr unsigned kFull = 0xffffffffu;
+enum { kModeHals = 0, kModeMu = 1, kModeStore = 2 };
+
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// dst(i, sum_c src(c, i)) for i < n4, c < cs, in a fixed order: the ranks are
+// split into NG contiguous groups summed by different threads (so all loads
+// are in flight at once), then the group sums are added in group order.
+// `scratch` holds NT float4.  Ends with every thread past a __syncthreads if NG > 1.
+template <typename Src, typename Dst>
+__device__ __forceinline__ void cluster_sum_f4(int n4, int cs, Src src, Dst dst, float4* scratch) {
+    const int NG = (n4 <= 0 || n4 >= NT) ? 1 : min(cs, NT / n4);
+    const int per = (cs + NG - 1) / NG;
+    for (int t = threadIdx.x; t < n4 * NG; t += NT) {
+        const int i = t % n4, grp = t / n4;
+        const int c0 = grp * per, c1 = min(cs, c0 + per);
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+        for (int c = c0; c < c1; ++c) s = f4add(s, src(c, i));
+        if (NG == 1)
+            dst(i, s);
+        else
+            scratch[t] = s;
+    }
+    if (NG > 1) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < n4; i += NT) {
+            float4 s = scratch[i];
+            for (int grp = 1; grp < NG; ++grp) s = f4add(s, scratch[grp * n4 + i]);
+            dst(i, s);
+        }
+    }
+}
+
+// Update of R rows of F (HALS or MU), RPW rows interleaved per warp.
+// Lane t owns the four consecutive entries k = 4t .. 4t+3 of each of its rows
+// (lanes 16..31 own nothing for r <= 64).  Inputs in shared memory (rows of
+// kMaxRank floats): Fn = incoming rows, Ared = product rows P_i, Dn = F_i G.
+// HALS walks the columns in the order k = 0, 1, ..., r-1 of Algorithm HALS:
+// the owner of a chunk runs its four steps on private copies (each step's
+// delta also corrects the owner's later entries of the chunk), broadcasts the
+// four deltas, and every lane applies them, in order, to its own entries.
+template <int RPW, int MODE>
+__device__ __forceinline__ void update_rows(float* __restrict__ F, int Na, int r, int rp, int R, int64_t rowbase,
+                                            float* Fn, const float* Ared, const float* Dn, const float* Gs,
+                                            const float* Ginv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = 4 * lane;
+    const bool has = c0 < r;
+    for (int base = warp * RPW; base < R; base += (NT / 32) * RPW) {
+        float f[RPW][4], g[RPW][4];
+        bool act[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int rr = base + q;
+            act[q] = rr < R && rowbase + rr < Na;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = c0 + e;
+                const bool ok = act[q] && k < r;
+                f[q][e] = ok ? Fn[rr * kMaxRank + k] : 0.f;
+                const float pv = ok ? Ared[rr * kMaxRank + k] : 0.f;
+                const float dv = ok ? Dn[rr * kMaxRank + k] : 0.f;
+                g[q][e] = MODE == kModeHals ? pv - dv : pv;
+                if (MODE == kModeMu) g[q][e] = ok ? f[q][e] * pv / fmaxf(dv, 1e-30f) : 0.f;
+            }
+        }
+        if (MODE == kModeHals) {
+            const int nchunks = (r + 3) / 4;
+            for (int t = 0; t < nchunks; ++t) {
+                // this lane's columns of the Gram rows 4t .. 4t+3
+                float Gk[4][4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int kk = 4 * t + e;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (kk < r && c0 < rp) v = *reinterpret_cast<const float4*>(Gs + kk * rp + c0);
+                    Gk[e][0] = v.x;
+                    Gk[e][1] = v.y;
+                    Gk[e][2] = v.z;
+                    Gk[e][3] = v.w;
+                }
+                const float4 gi4 = *reinterpret_cast<const float4*>(Ginv + 4 * t);
+                const float gi[4] = {gi4.x, gi4.y, gi4.z, gi4.w};
+                const bool own = lane == t;
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) {
+                    // the owner's four sequential steps (computed by every lane on its own
+                    // copies; only lane t's results are used)
+                    float gt[4] = {g[q][0], g[q][1], g[q][2], g[q][3]};
+                    float ft[4] = {f[q][0], f[q][1], f[q][2], f[q][3]};
+                    float dl[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float nv = fmaxf(0.f, fmaf(gt[e], gi[e], ft[e]));
+                        dl[e] = nv - ft[e];
+                        ft[e] = nv;
+#pragma unroll
+                        for (int e2 = e + 1; e2 < 4; ++e2) gt[e2] = fmaf(-dl[e], Gk[e][e2], gt[e2]);
+                    }
+                    float d[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) d[e] = __shfl_sync(kFull, dl[e], t);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        f[q][j] = own ? ft[j] : f[q][j];
+                        float gj = g[q][j];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) gj = fmaf(-d[e], Gk[e][j], gj);
+                        g[q][j] = gj;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < RPW; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) f[q][e] = g[q][e];
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int rr = base + q;
+            if (rr < R && c0 < kMaxRank)
+                *reinterpret_cast<float4*>(Fn + rr * kMaxRank + c0) =
+                    act[q] ? make_float4(f[q][0], f[q][1], f[q][2], f[q][3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (act[q] && has) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (c0 + e < r) F[(rowbase + rr) * rp + c0 + e] = f[q][e];
+            }
+        }
+    }
+}
+
+
+}  // namespace rowupd
+}  // namespace nmfk

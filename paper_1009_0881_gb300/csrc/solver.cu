@@ -18,12 +18,13 @@
 
 #include "fused.cuh"
 #include "nmf_internal.cuh"
+#include "tc_gemm.cuh"
 
 using namespace nmfk;
 
 namespace {
 
-const char* kBuildTag = "gb300-nmf sm_103a fp32-ffma";
+const char* kBuildTag = "gb300-nmf sm_103a fp32-ffma+bf16-tcgen05";
 
 // ---------------------------------------------------------------------------
 // Cycle schedules (Section 4.3) as a flat list of operations
@@ -116,6 +117,13 @@ struct Level {
     GemmTask tA{}, tB{}, tC{}, tD{};  // split-K products (nmf_products)
     HalfSweepLaunch hsV{}, hsW{};     // fused half-sweeps of the solve
     int gd_count = 0;                 // D partial slabs written by the V-step (64-row tiles of V)
+    // BF16 precision form: operand copies, descriptors and tcgen05 products
+    __nv_bfloat16* Mb = nullptr;   // m x ldmb
+    __nv_bfloat16* Mtb = nullptr;  // n x ldmtb
+    __nv_bfloat16* Vtb = nullptr;  // r x ldmtb (V transposed)
+    int64_t ldmtb = 0;
+    CUtensorMap tmVa{}, tmVb{}, tmWa{}, tmWb{};
+    TcGemmParams gV{}, gW{};
 };
 
 struct Plan {
@@ -142,6 +150,14 @@ struct Plan {
     unsigned long long* d_bad = nullptr;
     int64_t trace_cap = 0;
     size_t bytes = 0;
+    // BF16 precision form
+    bool bf16 = false;
+    int bn = 0;                       // MMA N
+    int64_t ldmb = 0;                 // leading dimension of M and W in BF16 (multiple of 8)
+    __nv_bfloat16* Wb = nullptr;      // r x ldmb
+    float* P1b = nullptr;             // split partials of A = M W^T
+    float* P2b = nullptr;             // split partials of C^T = M^T V
+    float* Gfin = nullptr;            // reduced Gram matrix, r x rp
 };
 
 }  // namespace
@@ -290,6 +306,42 @@ void layout(Plan& p, Bump& b, int num_sms) {
     p.d_trace = b.take<double>((size_t)(p.trace_cap > 0 ? p.trace_cap : 1));
     p.d_status = b.take<int>(1);
     p.d_bad = b.take<unsigned long long>(1);
+    if (p.bf16) {
+        p.bn = tc_block_n(p.r);
+        p.ldmb = round_up(n, 8);
+        p.Wb = b.take<__nv_bfloat16>((size_t)(p.r * p.ldmb));
+        p.Gfin = b.take<float>((size_t)p.slab);
+        int64_t max_p1b = 0, max_p2b = 0;
+        for (int l = 0; l < p.L; ++l) {
+            Level& v = p.lv[l];
+            v.ldmtb = round_up(v.m, 8);
+            v.Mb = b.take<__nv_bfloat16>((size_t)(v.m * p.ldmb));
+            v.Mtb = b.take<__nv_bfloat16>((size_t)(n * v.ldmtb));
+            v.Vtb = b.take<__nv_bfloat16>((size_t)(p.r * v.ldmtb));
+            v.gV = TcGemmParams{};
+            v.gV.Ma = (int)v.m;
+            tc_gemm_plan(v.gV, n, num_sms);
+            v.gV.ldo = rp;
+            v.gV.split_stride = v.m * rp;
+            v.gV.ncols = (int)rp;
+            v.gW = TcGemmParams{};
+            v.gW.Ma = (int)n;
+            tc_gemm_plan(v.gW, v.m, num_sms);
+            v.gW.ldo = rp;
+            v.gW.split_stride = n * rp;
+            v.gW.ncols = (int)rp;
+            max_p1b = std::max<int64_t>(max_p1b, v.gV.splits * v.gV.split_stride);
+            max_p2b = std::max<int64_t>(max_p2b, v.gW.splits * v.gW.split_stride);
+        }
+        p.P1b = b.take<float>((size_t)max_p1b);
+        p.P2b = b.take<float>((size_t)max_p2b);
+        for (int l = 0; l < p.L; ++l) {
+            p.lv[l].gV.out = p.P1b;
+            p.lv[l].gV.err_flag = p.err_flag;
+            p.lv[l].gW.out = p.P2b;
+            p.lv[l].gW.err_flag = p.err_flag;
+        }
+    }
     for (int l = 0; l < p.L; ++l) {
         Level& v = p.lv[l];
         v.tA.X = v.Mt;
@@ -393,6 +445,14 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
         e = make_tmap_f32(&b.tmX, v.M, p.n, v.m, p.ldm, 64, ks);
         if (e == cudaSuccess) e = make_tmap_f32(&b.tmY, v.V, p.rp, v.m, p.rp, p.br, ks);
         if (e != cudaSuccess) return fail(h, NMF_ECUDA, "TMA descriptor (W-step) failed: %s", cudaGetErrorString(e));
+        if (p.bf16) {
+            // tcgen05 operands: A tiles 128 rows x 64 K, B tiles bn rows x 64 K
+            e = make_tmap_bf16_sw128(&v.tmVa, v.Mb, p.n, v.m, p.ldmb, 128);
+            if (e == cudaSuccess) e = make_tmap_bf16_sw128(&v.tmVb, p.Wb, p.n, p.r, p.ldmb, p.bn);
+            if (e == cudaSuccess) e = make_tmap_bf16_sw128(&v.tmWa, v.Mtb, v.m, p.n, v.ldmtb, 128);
+            if (e == cudaSuccess) e = make_tmap_bf16_sw128(&v.tmWb, v.Vtb, v.m, p.r, v.ldmtb, p.bn);
+            if (e != cudaSuccess) return fail(h, NMF_ECUDA, "TMA descriptor (BF16) failed: %s", cudaGetErrorString(e));
+        }
     }
     return NMF_OK;
 }
@@ -402,6 +462,7 @@ int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, 
     p.n = n;
     p.r = r;
     p.rp = (int)round_up(r, 4);
+    p.bf16 = h->prec == NMF_BF16;
     p.br = pick_br(p.rp);
     p.L = L;
     p.ldm = round_up(n, 4);
@@ -497,7 +558,89 @@ cudaError_t enqueue_hierarchy(nmf_ctx* h, const Plan& p) {
         e = copy2d_launch(c.M, p.ldm, c.m, p.n, c.Mt, c.ldmt, true, h->stream);
         if (e != cudaSuccess) return e;
     }
+    if (p.bf16) {
+        // BF16 operand copies of every level (the objective stays on the FP32 M)
+        for (int l = 0; l < p.L; ++l) {
+            const Level& v = p.lv[l];
+            cudaError_t e = to_bf16_launch(v.M, p.ldm, v.m, p.n, v.Mb, p.ldmb, false, h->stream);
+            if (e == cudaSuccess) e = to_bf16_launch(v.M, p.ldm, v.m, p.n, v.Mtb, v.ldmtb, true, h->stream);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = to_bf16_launch(p.Wt, p.rp, p.n, p.r, p.Wb, p.ldmb, true, h->stream);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
+}
+
+// One sweep of the BF16 precision form at level l: tcgen05 product of the
+// V-step (split partials), final B from its slabs, row update of V (FP32 rows,
+// BF16 V^T, D slabs); then the same for the W-step.
+cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo) {
+    const Level& v = p.lv[l];
+    const int mode = algo == NMF_HALS ? 0 : (algo == NMF_MU ? 1 : 2);
+    cudaError_t e = tc_gemm_launch(p.bn, v.tmVa, v.tmVb, v.gV, h->stream);
+    if (e == cudaSuccess) e = gram_final_launch(p.GB, p.gb_count, p.slab, p.r, p.rp, p.Gfin, h->stream);
+    if (e != cudaSuccess) return e;
+    RowsParams q{};
+    q.F = v.V;
+    q.rows = v.m;
+    q.r = p.r;
+    q.rp = p.rp;
+    q.P = p.P1b;
+    q.ps = v.gV.split_stride;
+    q.splits = v.gV.splits;
+    q.G = p.Gfin;
+    q.Fb = v.Vtb;
+    q.ldb = v.ldmtb;
+    q.Gout = p.GD;
+    q.gout_stride = p.slab;
+    if (algo == NMF_ANLS) {
+        UpdateArgs u{};
+        u.F = v.V;
+        u.ldf = p.rp;
+        u.P = p.P1b;
+        u.ps = v.gV.split_stride;
+        u.ldp = p.rp;
+        u.splits = v.gV.splits;
+        u.PG = p.GB;
+        u.pgs = p.slab;
+        u.ldpg = p.rp;
+        u.gsplits = p.gb_count;
+        u.rows = v.m;
+        u.r = p.r;
+        e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    e = rows_update_launch(q, mode, h->stream);
+    if (e == cudaSuccess) e = tc_gemm_launch(p.bn, v.tmWa, v.tmWb, v.gW, h->stream);
+    if (e == cudaSuccess) e = gram_final_launch(p.GD, v.gd_count, p.slab, p.r, p.rp, p.Gfin, h->stream);
+    if (e != cudaSuccess) return e;
+    q.F = p.Wt;
+    q.rows = p.n;
+    q.P = p.P2b;
+    q.ps = v.gW.split_stride;
+    q.splits = v.gW.splits;
+    q.Fb = p.Wb;
+    q.ldb = p.ldmb;
+    q.Gout = p.GB;
+    if (algo == NMF_ANLS) {
+        UpdateArgs u{};
+        u.F = p.Wt;
+        u.ldf = p.rp;
+        u.P = p.P2b;
+        u.ps = v.gW.split_stride;
+        u.ldp = p.rp;
+        u.splits = v.gW.splits;
+        u.PG = p.GD;
+        u.pgs = p.slab;
+        u.ldpg = p.rp;
+        u.gsplits = v.gd_count;
+        u.rows = p.n;
+        u.r = p.r;
+        e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return rows_update_launch(q, mode, h->stream);
 }
 
 cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& ops, nmf_algo algo,
@@ -517,7 +660,7 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
         } else {
             for (int64_t s = 0; s < op.count; ++s) {
                 if (stop_after > 0 && done >= stop_after) break;
-                e = enqueue_sweep(h, p, op.level, algo, &launches);
+                e = p.bf16 ? enqueue_sweep_bf16(h, p, op.level, algo) : enqueue_sweep(h, p, op.level, algo, &launches);
                 if (e != cudaSuccess) return e;
                 ++done;
                 if (op.level == 0) {
@@ -609,7 +752,6 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     if (cyc != NMF_VCYCLE && cyc != NMF_NESTED && cyc != NMF_FMG) return fail(h, NMF_EINVAL, "unknown cycle");
     const int64_t stop_after = opt ? opt->stop_after : 0;
     const bool trace = opt && opt->trace && opt->trace_len > 0;
-    if (h->prec != NMF_FP32) return fail(h, NMF_EINVAL, "only the FP32 storage precision is built");
     CK(cudaSetDevice(h->device));
     h->launches = 0;
 
@@ -715,7 +857,8 @@ int nmf_create(nmf_handle* out, int device, size_t hbm_budget_bytes, nmf_precisi
         return NMF_ECUDA;
     }
     h->stream = h->own_stream;
-    if (init_kernel_attributes() != cudaSuccess || tma_init() != cudaSuccess || half_sweep_init() != cudaSuccess) {
+    if (init_kernel_attributes() != cudaSuccess || tma_init() != cudaSuccess || half_sweep_init() != cudaSuccess ||
+        tc_gemm_init() != cudaSuccess || rows_update_init() != cudaSuccess) {
         cudaGetLastError();
         nmf_destroy(h);
         return NMF_ECUDA;
@@ -818,6 +961,15 @@ int nmf_products(nmf_handle h, const float* M, const float* V, const float* W, i
     b2.t[1] = v.tD;
     b2.ntasks = 2;
     KL(1, gemm_tn_launch(b2, p.br, h->stream));
+    if (p.bf16) {
+        // precision form: A and C from BF16 copies of M, W and V on the tensor cores
+        KL(1, to_bf16_launch(v.M, p.ldm, m, n, v.Mb, p.ldmb, false, h->stream));
+        KL(1, to_bf16_launch(v.M, p.ldm, m, n, v.Mtb, v.ldmtb, true, h->stream));
+        KL(1, to_bf16_launch(p.Wt, p.rp, n, r, p.Wb, p.ldmb, true, h->stream));
+        KL(1, to_bf16_launch(v.V, p.rp, m, r, v.Vtb, v.ldmtb, true, h->stream));
+        KL(1, tc_gemm_launch(p.bn, v.tmVa, v.tmVb, v.gV, h->stream));
+        KL(1, tc_gemm_launch(p.bn, v.tmWa, v.tmWb, v.gW, h->stream));
+    }
     // reduce the split-K slabs into dense outputs, staged through tmp
     struct Out {
         float* dst;
@@ -826,9 +978,11 @@ int nmf_products(nmf_handle h, const float* M, const float* V, const float* W, i
         int splits;
         int64_t rows, cols;
         bool transpose;
-    } outs[4] = {{A, p.P1, v.tA.split_stride, v.tA.splits, m, r, false},
+    } outs[4] = {{A, p.bf16 ? p.P1b : p.P1, p.bf16 ? v.gV.split_stride : v.tA.split_stride,
+                  p.bf16 ? v.gV.splits : v.tA.splits, m, r, false},
                  {B, p.PG1, v.tB.split_stride, v.tB.splits, r, r, false},
-                 {C, p.P2, v.tC.split_stride, v.tC.splits, n, r, true},
+                 {C, p.bf16 ? p.P2b : p.P2, p.bf16 ? v.gW.split_stride : v.tC.split_stride,
+                  p.bf16 ? v.gW.splits : v.tC.splits, n, r, true},
                  {D, p.PG2, v.tD.split_stride, v.tD.splits, r, r, false}};
     for (const Out& o : outs) {
         if (!o.dst) continue;
@@ -908,6 +1062,12 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
     KL(1, gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.GB, p.slab, h->stream));
     const Level& v = p.lv[0];
     const int mode = algo == NMF_HALS ? kModeHals : (algo == NMF_MU ? kModeMu : kModeStore);
+    if (p.bf16) {
+        KL(1, to_bf16_launch(v.M, p.ldm, m, n, v.Mb, p.ldmb, false, h->stream));
+        KL(1, to_bf16_launch(v.M, p.ldm, m, n, v.Mtb, v.ldmtb, true, h->stream));
+        KL(1, to_bf16_launch(p.Wt, p.rp, n, r, p.Wb, p.ldmb, true, h->stream));
+        KL(1, to_bf16_launch(v.V, p.rp, m, r, v.Vtb, v.ldmtb, true, h->stream));
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -918,7 +1078,33 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
             if (it == 0) cudaEventRecord(e0, h->stream);
             cudaError_t e = cudaSuccess;
             int nl = 1;
-            if (phase == 0 || phase == 2) {
+            if (p.bf16 && phase < 4) {
+                // precision form: [0] tcgen05 V-step product, [1] Gram + V rows,
+                // [2] tcgen05 W-step product, [3] Gram + W rows
+                const bool vstep = phase < 2;
+                if (phase == 0 || phase == 2) {
+                    e = vstep ? tc_gemm_launch(p.bn, v.tmVa, v.tmVb, v.gV, h->stream)
+                              : tc_gemm_launch(p.bn, v.tmWa, v.tmWb, v.gW, h->stream);
+                } else {
+                    e = gram_final_launch(vstep ? p.GB : p.GD, vstep ? p.gb_count : v.gd_count, p.slab, p.r, p.rp,
+                                          p.Gfin, h->stream);
+                    RowsParams q{};
+                    q.F = vstep ? v.V : p.Wt;
+                    q.rows = vstep ? v.m : p.n;
+                    q.r = p.r;
+                    q.rp = p.rp;
+                    q.P = vstep ? p.P1b : p.P2b;
+                    q.ps = vstep ? v.gV.split_stride : v.gW.split_stride;
+                    q.splits = vstep ? v.gV.splits : v.gW.splits;
+                    q.G = p.Gfin;
+                    q.Fb = vstep ? v.Vtb : p.Wb;
+                    q.ldb = vstep ? v.ldmtb : p.ldmb;
+                    q.Gout = vstep ? p.GD : p.GB;
+                    q.gout_stride = p.slab;
+                    if (e == cudaSuccess) e = rows_update_launch(q, mode == kModeStore ? 2 : mode, h->stream);
+                    nl = 2;
+                }
+            } else if (phase == 0 || phase == 2) {
                 HalfSweepLaunch hl = phase == 0 ? v.hsV : v.hsW;
                 hl.mode = mode;
                 e = half_sweep_launch(hl, h->stream);

@@ -31,6 +31,9 @@ CASES = [
     ("grid16_hals_fmg_L3_K100", "grid16_n1000_r10", "hals", 3, 100, "fmg"),
     ("grid16_hals_ni_L3_K100", "grid16_n1000_r10", "hals", 3, 100, "ni"),
     ("grid16_mu_fmg_L3_K100", "grid16_n1000_r10", "mu", 3, 100, "fmg"),
+    # precision-form workloads (ORL shape; 256 x 256 grid)
+    ("grid112x92_hals_L3_K100", "grid112x92_n400_r40", "hals", 3, 100, "vcycle"),
+    ("grid256_hals_L3_K20", "grid256_n2000_r64", "hals", 3, 20, "vcycle"),
 ]
 
 

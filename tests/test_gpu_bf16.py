@@ -1,0 +1,120 @@
+"""GPU parity of the BF16 precision form (tcgen05 products).
+
+The precision form stores M and the product operands in bfloat16 and
+accumulates in FP32; the Gram matrices W W^T and V^T V and the factor updates
+stay FP32.  Its exact definition, used as the expected value here:
+    A = bf16(M) bf16(W)^T,  B = W W^T,   V-step of Algorithm HALS,
+    C = bf16(V)^T bf16(M),  D = V^T V,   W-step of Algorithm HALS,
+with the products evaluated in FP64 on the rounded operands.  Tolerances:
+  * products: the operands are exact, only FP32 accumulation differs: 1e-5;
+  * one sweep against that definition: V 1e-5; W 5e-4.  The GPU's float32 V
+    differs from the FP64 one by ~1e-6, so a fraction ~1e-6 / 2^-8 of the
+    entries of bf16(V) round to the neighbouring bfloat16 value; those flips
+    move C by ~sqrt(2.5e-4) * 2^-8 ~ 6e-5 and W by ~1e-4 (measured 1.0e-4);
+  * whole cycles against the FP64 oracle on the FP32 data: the objective is
+    within 2e-2 relative.  This is the bfloat16 storage floor (unit roundoff
+    2^-8 on M and on the product operands, rms ~1.1e-3 per entry, added to a
+    ~1 % residual); measured 1.1 % on the 112 x 92 grid and below 1e-2 on
+    the others.  The bench reports the measured difference.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import nmf_oracle as o
+from paper_1009_0881_gb300 import native, synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = json.load(open(os.path.join(ROOT, "tests", "golden", "objectives.json")))
+
+
+def bf16(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+@pytest.fixture(scope="module")
+def hb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1009_0881_gb300 import build
+    build.build()
+    with native.Handle(0, precision=native.NMF_BF16) as h:
+        yield h
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("m,n,r", [(361, 2429, 49), (10304, 400, 40), (100, 37, 5), (1000, 130, 17),
+                                   (16384, 2000, 64), (25, 2429, 49), (7, 9, 1)])
+def test_tensor_core_products(hb, m, n, r):
+    rng = np.random.default_rng(m * 7 + n + r)
+    M = rng.random((m, n)).astype(np.float32)
+    V = rng.random((m, r)).astype(np.float32)
+    W = rng.random((r, n)).astype(np.float32)
+    A = np.zeros((m, r), np.float32)
+    C = np.zeros((r, n), np.float32)
+    hb.products(M, V, W, A=A, C=C)
+    Mb, Vb, Wb = bf16(M).astype(np.float64), bf16(V).astype(np.float64), bf16(W).astype(np.float64)
+    assert rel(A, Mb @ Wb.T) < 1e-5
+    assert rel(C, Vb.T @ Mb) < 1e-5
+
+
+def _sweep_definition(M, V, W):
+    """One HALS sweep of the precision form, in FP64 on the rounded operands."""
+    V = V.astype(np.float64).copy()
+    W = W.astype(np.float64).copy()
+    Mb = bf16(M).astype(np.float64)
+    A = Mb @ bf16(W).astype(np.float64).T
+    B = W @ W.T
+    for k in range(V.shape[1]):
+        o.hals_update_V_column(V, A, B, k)
+    C = bf16(V).astype(np.float64).T @ Mb
+    D = V.T @ V
+    for k in range(W.shape[0]):
+        o.hals_update_W_row(W, C, D, k)
+    return V, W
+
+
+@pytest.mark.parametrize("wl", ["grid19_n2429_r49", "grid16_n1000_r10", "grid112x92_n400_r40"])
+def test_single_bf16_sweep_matches_definition(hb, wl):
+    gh, gw, n, r, sigma = synth.WORKLOADS[wl]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    V, W = p.V.copy(), p.W.copy()
+    hb.sweep(p.M, V, W, "hals", 1)
+    Ve, We = _sweep_definition(p.M, p.V, p.W)
+    assert rel(V, Ve) < 1e-5
+    assert rel(W, We) < 5e-4
+
+
+@pytest.mark.parametrize("name,tol", [("grid19_hals_L3_K500", 2e-2), ("grid16_hals_L3_K100", 2e-2),
+                                      ("grid19_mu_L3_K500", 2e-2), ("grid112x92_hals_L3_K100", 2e-2),
+                                      ("grid256_hals_L3_K20", 2e-2)])
+def test_bf16_cycle_objective_near_fp64_oracle(hb, name, tol):
+    g = GOLDEN[name]
+    gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    V, W = p.V.copy(), p.W.copy()
+    hb.solve(p.M, gh, gw, V, W, g["algo"], levels=g["levels"], iters=g["K"], cycle=g["cycle"])
+    f = o.objective(p.M, V, W)  # against the FP32 data, never the BF16 copy
+    assert abs(f - g["objective"]) <= tol * g["objective"], (f, g["objective"])
+    assert (V >= 0).all() and (W >= 0).all()
+
+
+def test_bf16_anls_sweep_is_blockwise_optimal(hb):
+    # ANLS on BF16 products: the V-step is the exact NNLS solution for A = bf16(M) bf16(W)^T, B = W W^T
+    p = synth.make_problem(16, 16, 300, 8, data_seed=3)
+    V, W = p.V.copy(), p.W.copy()
+    hb.sweep(p.M, V, W, "anls", 1)
+    A = bf16(p.M).astype(np.float64) @ bf16(p.W).astype(np.float64).T
+    B = p.W.astype(np.float64) @ p.W.astype(np.float64).T
+    Ve = np.stack([o.nnls_active_set(B, A[i]) for i in range(A.shape[0])])
+    assert rel(V, Ve) < 1e-4
