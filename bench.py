@@ -450,7 +450,7 @@ def roofline(args, h, Md, gh, gw, n, r, sched):
     return roof, times
 
 
-PRECISION_WORKLOADS = [("grid112x92_n400_r40", 3, 100), ("grid256_n2000_r64", 3, 20)]
+PRECISION_WORKLOADS = [("grid112x92_n400_r40", 3, 100), ("grid256_n2000_r64", 3, 100)]
 
 
 def precision_form(args, reps=3):

@@ -115,6 +115,38 @@ int nmf_solve_ex(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h,
                  int r, nmf_algo algo, int levels, int iters, const nmf_options* opt,
                  float* V, float* W);
 
+/* One problem of a batched solve (nmf_solve_batch). */
+typedef struct {
+    const float* M;    /* m x n, >= 0, host or device */
+    int64_t m, n;
+    int grid_h, grid_w; /* grid_h * grid_w == m */
+    int r;
+    nmf_algo algo;
+    int levels, iters;  /* cycle levels L and sweep budget K, as in nmf_solve */
+    nmf_cycle cycle;
+    double rel_tol;     /* > 0: stopping rule on the last run of finest-level sweeps (the
+                           post-smoothing of a V-cycle): stop once |f_{t-1} - f_t| <= rel_tol * f_t,
+                           f_t = ||M - VW||_F after finest-level sweep t (HALS and MU; ignored for
+                           ANLS); 0: run the whole schedule */
+    float* V;           /* in: V0 (m x r); out: result */
+    float* W;           /* in: W0 (r x n); out: result */
+    /* outputs */
+    int status;         /* nmf_status of this problem */
+    int64_t sweeps_run; /* sweeps executed over all levels */
+    double objective;   /* ||M - VW||_F of the result, FP64 accumulation */
+} nmf_problem;
+
+/*
+ * nmf_solve_batch - solve `count` independent problems (any mix of sizes, ranks
+ * and algorithms) at once: all of them are planned into one workspace and their
+ * schedules recorded as concurrent branches of one CUDA graph, so the device
+ * overlaps their kernels.  Each problem's result equals what nmf_solve would
+ * return for it alone (same kernels, same launch shapes, same summation order),
+ * up to the stopping rule.  Returns NMF_OK if every problem succeeded, else the
+ * first failing status (per-problem statuses in probs[i].status).
+ */
+int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count);
+
 /*
  * nmf_error - ||M - VW||_F (problem (NMF), Section 2) with float32 products and
  * FP64 accumulation of the squared residuals.  *err_out receives the value

@@ -47,9 +47,10 @@ __global__ void to_bf16_t_kernel(const float* __restrict__ in, int64_t ldi, int6
     }
 }
 
-__global__ void gram_final_kernel(const float* __restrict__ slabs, int count, int64_t stride, int n, float* __restrict__ G) {
+__global__ void gram_final_kernel(const float* __restrict__ slabs, int count, int64_t stride, int n,
+                                  float* __restrict__ G, const int* skip) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
+    if (e >= n || (skip && *(volatile const int*)skip)) return;
     float s = 0.f;
     for (int q = 0; q < count; ++q) s += slabs[(int64_t)q * stride + e];
     G[e] = s;
@@ -58,6 +59,7 @@ __global__ void gram_final_kernel(const float* __restrict__ slabs, int count, in
 template <int MODE>
 __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) {
     extern __shared__ __align__(16) float sm[];
+    if (q.skip && *(volatile const int*)q.skip) return;  // converged problem: nothing to do
     const int r = q.r, rp = q.rp;
     float* Gs = sm;                       // r x rp
     float* Ginv = Gs + r * rp;            // kMaxRank
@@ -180,9 +182,10 @@ cudaError_t to_bf16_launch(const float* in, int64_t ldi, int64_t rows, int64_t c
     return cudaGetLastError();
 }
 
-cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int r, int rp, float* G, cudaStream_t st) {
+cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int r, int rp, float* G, cudaStream_t st,
+                              const int* skip) {
     const int n = r * rp;
-    gram_final_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(slabs, count, stride, n, G);
+    gram_final_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(slabs, count, stride, n, G, skip);
     return cudaGetLastError();
 }
 

@@ -131,19 +131,27 @@ __global__ void __launch_bounds__(NT, 1)
     }
     __syncthreads();
     // X (M or its transpose) is constant during the sweeps: its first stages load
-    // while the previous half-sweep may still be finishing (programmatic launch)
-    if (tid == 0) {
+    // while the previous half-sweep may still be finishing (programmatic launch).
+    // A launch that may be skipped issues nothing before it has read its flag.
+    const bool early_x = p.skip == nullptr;
+    if (early_x && tid == 0) {
         for (int s = 0; s < NST && s < nst; ++s) {
             ptx::mbar_arrive_expect_tx(&bar[s], kStageBytes);
             ptx::tma_load_2d(Xs + s * KS * BA, &tmX, &bar[s], a0, (int)(k0 + s * KS));
         }
     }
-    // everything below reads what the previous kernel wrote (Y, F, Gram slabs)
+    // everything below reads what the previous kernel wrote (Y, F, Gram slabs, flag)
     ptx::grid_dependency_wait();
     ptx::launch_dependents();
+    if (p.skip && *(volatile const int*)p.skip) return;  // same value in every CTA of the grid
     if (tid == 0) {
-        for (int s = 0; s < NST && s < nst; ++s)
+        for (int s = 0; s < NST && s < nst; ++s) {
+            if (!early_x) {
+                ptx::mbar_arrive_expect_tx(&bar[s], kStageBytes);
+                ptx::tma_load_2d(Xs + s * KS * BA, &tmX, &bar[s], a0, (int)(k0 + s * KS));
+            }
             ptx::tma_load_2d(Ys + s * KS * BR, &tmY, &bar[s], 0, (int)(k0 + s * KS));
+        }
     }
 
     // ---- the incoming rows of F that this CTA updates, copied asynchronously

@@ -24,6 +24,7 @@ struct HalfSweepParams {
     int64_t gout_stride;
     float* Pout;       // STORE mode: reduced product rows, Na x rp
     int* err_flag;     // set to 1 if a bounded wait gave up
+    const int* skip;   // optional: when *skip != 0 the launch does nothing (converged problem)
 };
 
 struct HalfSweepLaunch {

@@ -109,6 +109,9 @@ cudaError_t check_nonneg_launch(const float* X, int64_t ld, int64_t rows, int64_
 // sums per CTA into d_partials (size >= error_partials_needed()), the norm into d_out.
 // ---------------------------------------------------------------------------
 int64_t error_partials_needed(int64_t m, int64_t n);
+// Batched stopping rule: sets *flag once |f_prev - f_now| <= tol * f_now; counts sweeps run.
+cudaError_t converge_check_launch(const double* f_now, double* state, int* flag, double tol, long long* count,
+                                  cudaStream_t st);
 cudaError_t error_launch(const float* M, int64_t ldm, const float* V, const float* Wt, int64_t rp,
                          int64_t m, int64_t n, int r, double* d_partials, double* d_out,
                          cudaStream_t st);

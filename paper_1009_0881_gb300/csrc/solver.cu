@@ -158,6 +158,10 @@ struct Plan {
     float* P1b = nullptr;             // split partials of A = M W^T
     float* P2b = nullptr;             // split partials of C^T = M^T V
     float* Gfin = nullptr;            // reduced Gram matrix, r x rp
+    // stopping rule of the batched form
+    double* conv_state = nullptr;     // [0] previous objective, [1] current, [2] final
+    int* conv_flag = nullptr;
+    long long* conv_count = nullptr;  // finest-level sweeps run under the rule
 };
 
 }  // namespace
@@ -185,6 +189,8 @@ struct nmf_ctx {
     int* h_flag = nullptr;
     double* h_err = nullptr;
     std::map<std::string, GraphEntry> graphs;
+    std::vector<cudaStream_t> branch_streams;  // capture branches of batched solves
+    std::vector<cudaEvent_t> branch_events;
 };
 
 namespace {
@@ -306,6 +312,9 @@ void layout(Plan& p, Bump& b, int num_sms) {
     p.d_trace = b.take<double>((size_t)(p.trace_cap > 0 ? p.trace_cap : 1));
     p.d_status = b.take<int>(1);
     p.d_bad = b.take<unsigned long long>(1);
+    p.conv_state = b.take<double>(3);
+    p.conv_flag = b.take<int>(1);
+    p.conv_count = b.take<long long>(1);
     if (p.bf16) {
         p.bn = tc_block_n(p.r);
         p.ldmb = round_up(n, 8);
@@ -457,7 +466,48 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
     return NMF_OK;
 }
 
+void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap);
+
+// Plans of several problems laid out back to back in the handle's workspace.
+int make_plans(nmf_ctx* h, std::vector<Plan>& plans) {
+    Bump dry;
+    for (Plan& p : plans) layout(p, dry, h->num_sms);
+    int rc = ensure_workspace(h, dry.off);
+    if (rc) return rc;
+    Bump real;
+    real.dry = false;
+    real.base = h->ws;
+    real.cap = h->ws_cap;
+    for (Plan& p : plans) {
+        layout(p, real, h->num_sms);
+        rc = plan_half_sweeps(h, p);
+        if (rc) return rc;
+    }
+    return NMF_OK;
+}
+
+// Workspace bytes the plans would need (no allocation).
+size_t plans_bytes(nmf_ctx* h, std::vector<Plan>& plans) {
+    Bump dry;
+    for (Plan& p : plans) layout(p, dry, h->num_sms);
+    return dry.off;
+}
+
 int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap) {
+    plan_dims(h, p, m, n, gh, gw, r, L, trace_cap);
+    Bump dry;
+    layout(p, dry, h->num_sms);
+    int rc = ensure_workspace(h, dry.off);
+    if (rc) return rc;
+    Bump real;
+    real.dry = false;
+    real.base = h->ws;
+    real.cap = h->ws_cap;
+    layout(p, real, h->num_sms);
+    return plan_half_sweeps(h, p);
+}
+
+void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap) {
     p.m = m;
     p.n = n;
     p.r = r;
@@ -476,16 +526,6 @@ int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, 
         hh = (hh + 1) / 2;
         ww = (ww + 1) / 2;
     }
-    Bump dry;
-    layout(p, dry, h->num_sms);
-    int rc = ensure_workspace(h, dry.off);
-    if (rc) return rc;
-    Bump real;
-    real.dry = false;
-    real.base = h->ws;
-    real.cap = h->ws_cap;
-    layout(p, real, h->num_sms);
-    return plan_half_sweeps(h, p);
 }
 
 // One sweep of the inner algorithm at level l: the V-step (products M W^T and
@@ -493,11 +533,13 @@ int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, 
 // slabs) and the W-step (products M^T V, reduction of the D slabs, new rows of
 // Wt and their B slabs).  HALS and MU update inside the fused kernel; ANLS
 // stores the reduced products and runs the active-set solver on them.
-cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64_t* launches) {
+cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64_t* launches,
+                          const int* skip = nullptr) {
     const Level& v = p.lv[l];
     const int mode = algo == NMF_HALS ? kModeHals : (algo == NMF_MU ? kModeMu : kModeStore);
     HalfSweepLaunch a = v.hsV;
     a.mode = mode;
+    a.p.skip = skip;
     cudaError_t e = half_sweep_launch(a, h->stream);
     if (e != cudaSuccess) return e;
     ++*launches;
@@ -522,6 +564,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
     }
     HalfSweepLaunch b = v.hsW;
     b.mode = mode;
+    b.p.skip = skip;
     e = half_sweep_launch(b, h->stream);
     if (e != cudaSuccess) return e;
     ++*launches;
@@ -575,11 +618,14 @@ cudaError_t enqueue_hierarchy(nmf_ctx* h, const Plan& p) {
 // One sweep of the BF16 precision form at level l: tcgen05 product of the
 // V-step (split partials), final B from its slabs, row update of V (FP32 rows,
 // BF16 V^T, D slabs); then the same for the W-step.
-cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo) {
+cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, const int* skip = nullptr) {
     const Level& v = p.lv[l];
     const int mode = algo == NMF_HALS ? 0 : (algo == NMF_MU ? 1 : 2);
-    cudaError_t e = tc_gemm_launch(p.bn, v.tmVa, v.tmVb, v.gV, h->stream);
-    if (e == cudaSuccess) e = gram_final_launch(p.GB, p.gb_count, p.slab, p.r, p.rp, p.Gfin, h->stream);
+    TcGemmParams gV = v.gV, gW = v.gW;
+    gV.skip = skip;
+    gW.skip = skip;
+    cudaError_t e = tc_gemm_launch(p.bn, v.tmVa, v.tmVb, gV, h->stream);
+    if (e == cudaSuccess) e = gram_final_launch(p.GB, p.gb_count, p.slab, p.r, p.rp, p.Gfin, h->stream, skip);
     if (e != cudaSuccess) return e;
     RowsParams q{};
     q.F = v.V;
@@ -594,6 +640,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo) 
     q.ldb = v.ldmtb;
     q.Gout = p.GD;
     q.gout_stride = p.slab;
+    q.skip = skip;
     if (algo == NMF_ANLS) {
         UpdateArgs u{};
         u.F = v.V;
@@ -612,8 +659,8 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo) 
         if (e != cudaSuccess) return e;
     }
     e = rows_update_launch(q, mode, h->stream);
-    if (e == cudaSuccess) e = tc_gemm_launch(p.bn, v.tmWa, v.tmWb, v.gW, h->stream);
-    if (e == cudaSuccess) e = gram_final_launch(p.GD, v.gd_count, p.slab, p.r, p.rp, p.Gfin, h->stream);
+    if (e == cudaSuccess) e = tc_gemm_launch(p.bn, v.tmWa, v.tmWb, gW, h->stream);
+    if (e == cudaSuccess) e = gram_final_launch(p.GD, v.gd_count, p.slab, p.r, p.rp, p.Gfin, h->stream, skip);
     if (e != cudaSuccess) return e;
     q.F = p.Wt;
     q.rows = p.n;
@@ -644,13 +691,20 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo) 
 }
 
 cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& ops, nmf_algo algo,
-                             int64_t stop_after, bool trace, int64_t* fine_sweeps) {
+                             int64_t stop_after, bool trace, int64_t* fine_sweeps, double rel_tol = 0.0) {
     int64_t done = 0, tidx = 0, launches = 0;
+    // the stopping rule (batched form) watches the last run of finest-level sweeps
+    int last_fine = -1;
+    for (int i = 0; i < (int)ops.size(); ++i)
+        if (ops[i].kind == OP_SWEEPS && ops[i].level == 0) last_fine = i;
+    const bool stop_rule = rel_tol > 0.0 && algo != NMF_ANLS && last_fine >= 0;
     // B = W W^T slabs of the initial W, consumed by the first V-step
     cudaError_t e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.GB, p.slab, h->stream);
     if (e != cudaSuccess) return e;
-    for (const Op& op : ops) {
+    for (int oi = 0; oi < (int)ops.size(); ++oi) {
+        const Op& op = ops[oi];
         const Level& f = p.lv[op.level];
+        const bool watched = stop_rule && oi == last_fine;
         if (op.kind == OP_RESTRICT_V) {
             const Level& c = p.lv[op.level + 1];
             e = restrict_launch(f.V, p.rp, f.h, f.w, p.rp, c.V, p.rp, h->stream);
@@ -660,9 +714,19 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
         } else {
             for (int64_t s = 0; s < op.count; ++s) {
                 if (stop_after > 0 && done >= stop_after) break;
-                e = p.bf16 ? enqueue_sweep_bf16(h, p, op.level, algo) : enqueue_sweep(h, p, op.level, algo, &launches);
+                const int* skip = watched ? p.conv_flag : nullptr;
+                e = p.bf16 ? enqueue_sweep_bf16(h, p, op.level, algo, skip)
+                           : enqueue_sweep(h, p, op.level, algo, &launches, skip);
                 if (e != cudaSuccess) return e;
                 ++done;
+                if (watched) {
+                    e = error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, f.m, p.n, p.r, p.err_part, p.conv_state + 1,
+                                     h->stream);
+                    if (e == cudaSuccess)
+                        e = converge_check_launch(p.conv_state + 1, p.conv_state, p.conv_flag, rel_tol, p.conv_count,
+                                                  h->stream);
+                    if (e != cudaSuccess) return e;
+                }
                 if (op.level == 0) {
                     if (trace && tidx < p.trace_cap) {
                         e = error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, f.m, p.n, p.r, p.err_part, p.d_trace + tidx,
@@ -825,6 +889,163 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     return NMF_OK;
 }
 
+constexpr int kBranchStreams = 16;
+
+int ensure_branches(nmf_ctx* h, int n) {
+    while ((int)h->branch_streams.size() < n) {
+        cudaStream_t s;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        h->branch_streams.push_back(s);
+    }
+    while ((int)h->branch_events.size() < n + 1) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->branch_events.push_back(e);
+    }
+    return NMF_OK;
+}
+
+int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
+    if (!h) return NMF_EINVAL;
+    if (!probs || count < 1) return fail(h, NMF_EINVAL, "empty batch");
+    for (int i = 0; i < count; ++i) {
+        const nmf_problem& q = probs[i];
+        int rc = check_dims(h, q.m, q.n, q.r);
+        if (rc) return rc;
+        if (!q.M || !q.V || !q.W) return fail(h, NMF_EINVAL, "problem %d: null pointer", i);
+        if (q.grid_h < 1 || q.grid_w < 1 || (int64_t)q.grid_h * q.grid_w != q.m)
+            return fail(h, NMF_EINVAL, "problem %d: grid does not have m pixels", i);
+        if (q.levels < 1 || q.levels > 16 || q.iters < 0) return fail(h, NMF_EINVAL, "problem %d: bad levels/iters", i);
+        if (q.algo != NMF_HALS && q.algo != NMF_MU && q.algo != NMF_ANLS)
+            return fail(h, NMF_EINVAL, "problem %d: unknown algorithm", i);
+        if (q.cycle != NMF_VCYCLE && q.cycle != NMF_NESTED && q.cycle != NMF_FMG)
+            return fail(h, NMF_EINVAL, "problem %d: unknown cycle", i);
+    }
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+    std::vector<Plan> plans(count);
+    for (int i = 0; i < count; ++i)
+        plan_dims(h, plans[i], probs[i].m, probs[i].n, probs[i].grid_h, probs[i].grid_w, probs[i].r, probs[i].levels, 0);
+    int rc = make_plans(h, plans);
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) {
+        rc = init_levels_padding(h, plans[i]);
+        if (rc) return rc;
+        rc = stage_problem(h, plans[i], probs[i].M, probs[i].V, probs[i].W);
+        if (rc) return rc;
+        Plan& p = plans[i];
+        CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(p.conv_state, 0, 3 * sizeof(double), h->stream));
+        CK(cudaMemsetAsync(p.conv_flag, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(p.conv_count, 0, sizeof(long long), h->stream));
+    }
+    const int nb = std::min(count, kBranchStreams);
+    rc = ensure_branches(h, nb);
+    if (rc) return rc;
+
+    // one graph: every problem's hierarchy, schedule and final objective on its own branch
+    std::string key = "batch";
+    char buf[160];
+    for (int i = 0; i < count; ++i) {
+        const nmf_problem& q = probs[i];
+        snprintf(buf, sizeof buf, ":%lld,%lld,%d,%d,%d,%d,%d,%d,%d,%.3g", (long long)q.m, (long long)q.n, q.grid_h,
+                 q.grid_w, q.r, (int)q.algo, q.levels, q.iters, (int)q.cycle, q.rel_tol);
+        key += buf;
+    }
+    snprintf(buf, sizeof buf, ":%p", (void*)h->ws);
+    key += buf;
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        GraphEntry ge;
+        cudaGraph_t graph = nullptr;
+        cudaStream_t main = h->stream;
+        CK(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaEventRecord(h->branch_events[nb], main);
+        for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(h->branch_streams[b], h->branch_events[nb], 0);
+        for (int i = 0; i < count && e == cudaSuccess; ++i) {
+            const nmf_problem& q = probs[i];
+            const Plan& p = plans[i];
+            h->stream = h->branch_streams[i % nb];
+            e = enqueue_hierarchy(h, p);
+            int64_t fine = 0;
+            if (e == cudaSuccess)
+                e = enqueue_schedule(h, p, build_schedule(q.cycle, q.levels, q.iters), q.algo, 0, false, &fine,
+                                     q.rel_tol);
+            if (e == cudaSuccess)
+                e = error_launch(p.lv[0].M, p.ldm, p.lv[0].V, p.Wt, p.rp, p.m, p.n, p.r, p.err_part,
+                                 p.conv_state + 2, h->stream);
+        }
+        for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+            e = cudaEventRecord(h->branch_events[b], h->branch_streams[b]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(main, h->branch_events[b], 0);
+        }
+        h->stream = main;
+        cudaError_t e2 = cudaStreamEndCapture(main, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(h, NMF_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        size_t nn = 0;
+        e = cudaGraphGetNodes(graph, nullptr, &nn);
+        if (e == cudaSuccess && nn) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+            for (size_t k = 0; e == cudaSuccess && k < nn; ++k) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++ge.kernels;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(h, NMF_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+        it = h->graphs.emplace(key, ge).first;
+    }
+    h->launches += it->second.kernels;
+    CK(cudaGraphLaunch(it->second.exec, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+
+    // per-problem results and statuses
+    int first_bad = NMF_OK;
+    for (int i = 0; i < count; ++i) {
+        nmf_problem& q = probs[i];
+        const Plan& p = plans[i];
+        unsigned long long bad = 0;
+        int st = 0, flag = 0;
+        long long cnt = 0;
+        double obj = 0.0;
+        CK(cudaMemcpy(&bad, p.d_bad, sizeof bad, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&st, p.d_status, sizeof st, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&flag, p.err_flag, sizeof flag, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&cnt, p.conv_count, sizeof cnt, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&obj, p.conv_state + 2, sizeof obj, cudaMemcpyDeviceToHost));
+        // sweeps: the whole schedule, minus the watched finest-level run replaced by its counted part
+        const std::vector<Op> ops = build_schedule(q.cycle, q.levels, q.iters);
+        int last_fine = -1;
+        int64_t total = 0;
+        for (int k = 0; k < (int)ops.size(); ++k)
+            if (ops[k].kind == OP_SWEEPS) {
+                total += ops[k].count;
+                if (ops[k].level == 0) last_fine = k;
+            }
+        if (q.rel_tol > 0.0 && q.algo != NMF_ANLS && last_fine >= 0) total += cnt - ops[last_fine].count;
+        q.sweeps_run = total;
+        q.objective = obj;
+        q.status = bad ? NMF_EINVAL : (flag ? NMF_ETIMEOUT : (st ? NMF_ENOCONV : NMF_OK));
+        if (!bad) {
+            CK(stage_out(h, p.lv[0].V, p.rp, q.m, q.r, q.V));
+            KL(1, copy2d_launch(p.Wt, p.rp, q.n, q.r, p.tmp, q.n, true, h->stream));
+            CK(stage_out(h, p.tmp, q.n, q.r, q.n, q.W));
+        }
+        if (q.status != NMF_OK && first_bad == NMF_OK) {
+            first_bad = q.status;
+            fail(h, q.status, "problem %d failed with status %d", i, q.status);
+        }
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return first_bad;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -876,6 +1097,8 @@ void nmf_destroy(nmf_handle h) {
     if (h->h_status) cudaFreeHost(h->h_status);
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->h_flag) cudaFreeHost(h->h_flag);
+    for (cudaStream_t s : h->branch_streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : h->branch_events) cudaEventDestroy(e);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
@@ -909,6 +1132,8 @@ int nmf_solve_ex(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h,
                  int levels, int iters, const nmf_options* opt, float* V, float* W) {
     return solve_impl(h, M, m, n, grid_h, grid_w, r, algo, levels, iters, opt, V, W);
 }
+
+int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count) { return batch_impl(h, probs, count); }
 
 int nmf_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo, int sweeps, float* V,
               float* W) {

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* done = empty + NSTAGE;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
+    if (p.skip && *(volatile const int*)p.skip) return;  // converged problem: nothing to do
     const int warp = threadIdx.x >> 5;
     const int m0 = blockIdx.x * TM_ROWS;
     const int split = blockIdx.y;

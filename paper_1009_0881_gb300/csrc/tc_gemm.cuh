@@ -19,6 +19,7 @@ struct TcGemmParams {
     int64_t ldo, split_stride;
     int ncols;              // output columns stored (multiple of 4)
     int* err_flag;
+    const int* skip;        // optional: when *skip != 0 the launch does nothing
 };
 
 cudaError_t tc_gemm_init();
@@ -36,7 +37,7 @@ cudaError_t to_bf16_launch(const float* in, int64_t ldi, int64_t rows, int64_t c
                            int64_t ldo, bool transpose, cudaStream_t st);
 // G[e] = sum over `count` slabs (stride `stride`) of slab[e], e < r * rp, fixed order
 cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int r, int rp, float* G,
-                              cudaStream_t st);
+                              cudaStream_t st, const int* skip = nullptr);
 
 struct RowsParams {
     float* F;              // rows x rp factor (FP32), updated in place
@@ -50,6 +51,7 @@ struct RowsParams {
     int64_t ldb;
     float* Gout;           // Gram slab of every 64-row tile of the new rows
     int64_t gout_stride;
+    const int* skip;       // optional: when *skip != 0 the launch does nothing
 };
 // mode: 0 HALS, 1 MU, 2 no update (copy + Gram slabs only)
 cudaError_t rows_update_launch(const RowsParams& q, int mode, cudaStream_t st);

@@ -319,4 +319,24 @@ cudaError_t error_launch(const float* M, int64_t ldm, const float* V, const floa
     return cudaGetLastError();
 }
 
+namespace {
+// Stopping rule of the batched form: after a finest-level sweep with objective
+// f_t, stop once |f_{t-1} - f_t| <= tol * f_t (state[0] holds f_{t-1}, 0 before
+// the first sweep).  Counts the sweeps that ran.
+__global__ void converge_check_kernel(const double* __restrict__ f_now, double* state, int* flag, double tol,
+                                      long long* count) {
+    if (*flag) return;
+    const double cur = *f_now, prev = state[0];
+    *count += 1;
+    if (prev > 0.0 && fabs(prev - cur) <= tol * cur) *flag = 1;
+    state[0] = cur;
+}
+}  // namespace
+
+cudaError_t converge_check_launch(const double* f_now, double* state, int* flag, double tol, long long* count,
+                                  cudaStream_t st) {
+    converge_check_kernel<<<1, 1, 0, st>>>(f_now, state, flag, tol, count);
+    return cudaGetLastError();
+}
+
 }  // namespace nmfk

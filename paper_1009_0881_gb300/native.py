@@ -44,7 +44,15 @@ SIGNATURES = [
     ("nmf_last_launch_count", _I64, [_P]),
     ("nmf_profile_sweep", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
     ("nmf_error_noalloc", _I, [_P, _P, _P, _I64, _I64, _I, _P, ctypes.POINTER(ctypes.c_double)]),
+    ("nmf_solve_batch", _I, [_P, _P, _I]),
 ]
+
+
+class Problem(ctypes.Structure):
+    """nmf_problem of include/nmf.h."""
+    _fields_ = [("M", _P), ("m", _I64), ("n", _I64), ("grid_h", _I), ("grid_w", _I), ("r", _I), ("algo", _I),
+                ("levels", _I), ("iters", _I), ("cycle", _I), ("rel_tol", ctypes.c_double), ("V", _P), ("W", _P),
+                ("status", _I), ("sweeps_run", _I64), ("objective", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):
@@ -168,6 +176,32 @@ class Handle:
         if trace is not None:
             return trace[: min(count.value, trace_len)]
         return None
+
+    def solve_batch(self, problems):
+        """nmf_solve_batch.  `problems`: list of dicts with keys M, grid_h, grid_w, V, W and optional
+        algo, levels, iters, cycle, rel_tol.  V and W are improved in place; returns a list of
+        (status, sweeps_run, objective)."""
+        arr = (Problem * len(problems))()
+        for q, d in zip(arr, problems):
+            _check_f32(d["M"], d["V"], d["W"])
+            q.M = _ptr(d["M"])
+            q.m, q.n = d["M"].shape
+            q.grid_h, q.grid_w = d["grid_h"], d["grid_w"]
+            q.r = d["V"].shape[1]
+            algo = d.get("algo", "hals")
+            q.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+            q.levels = d.get("levels", 1)
+            q.iters = d.get("iters", 100)
+            cyc = d.get("cycle", "vcycle")
+            q.cycle = CYCLES[cyc] if isinstance(cyc, str) else int(cyc)
+            q.rel_tol = d.get("rel_tol", 0.0)
+            q.V = _ptr(d["V"])
+            q.W = _ptr(d["W"])
+        rc = self.lib.nmf_solve_batch(self.h, ctypes.cast(arr, _P), len(problems))
+        out = [(q.status, q.sweeps_run, q.objective) for q in arr]
+        if rc != 0 and all(s == 0 for s, _, _ in out):
+            self._rc(rc)
+        return out
 
     def solve_plain(self, M, grid_h, grid_w, V, W, algo="hals", levels=1, iters=100):
         """nmf_solve (V-cycle, no options)."""

@@ -34,6 +34,7 @@ CASES = [
     # precision-form workloads (ORL shape; 256 x 256 grid)
     ("grid112x92_hals_L3_K100", "grid112x92_n400_r40", "hals", 3, 100, "vcycle"),
     ("grid256_hals_L3_K20", "grid256_n2000_r64", "hals", 3, 20, "vcycle"),
+    ("grid256_hals_L3_K100", "grid256_n2000_r64", "hals", 3, 100, "vcycle"),
 ]
 
 

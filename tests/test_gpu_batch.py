@@ -1,0 +1,124 @@
+"""GPU tests of the batched form (nmf_solve_batch): many uneven problems in one
+CUDA graph of concurrent branches.
+
+Required property: a problem's result is the same alone and in the batch.  The
+batch runs the same kernels with the same launch shapes and summation orders
+as nmf_solve, so the comparison is bitwise.  The stopping rule (relative
+objective change of consecutive finest-level post-smoothing sweeps) is checked
+against the per-sweep objective trace of the standalone solve.
+"""
+import numpy as np
+import pytest
+
+from oracle import nmf_oracle as o
+from paper_1009_0881_gb300 import native, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", params=[native.NMF_FP32, native.NMF_BF16], ids=["fp32", "bf16"])
+def h(request):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1009_0881_gb300 import build
+    build.build()
+    with native.Handle(0, precision=request.param) as hd:
+        yield hd
+
+
+MIX = [  # (side_h, side_w, n, r, algo, levels, iters)
+    (16, 16, 700, 10, "hals", 3, 40),
+    (19, 19, 2429, 49, "hals", 3, 20),
+    (32, 32, 300, 5, "mu", 3, 40),
+    (64, 64, 1200, 64, "hals", 2, 12),
+    (92, 92, 250, 23, "hals", 3, 16),
+    (16, 16, 900, 7, "mu", 1, 30),
+    (128, 128, 400, 33, "hals", 3, 8),
+]
+
+
+def _problems(seed0=0):
+    out = []
+    for i, (gh, gw, n, r, algo, L, K) in enumerate(MIX):
+        p = synth.make_problem(gh, gw, n, r, sigma=0.04 * gw if gw > 19 else 2.0, data_seed=seed0 + i)
+        out.append((p, algo, L, K))
+    return out
+
+
+def test_batch_equals_alone(h):
+    probs = _problems()
+    batch = []
+    for p, algo, L, K in probs:
+        batch.append(dict(M=p.M, grid_h=p.grid_h, grid_w=p.grid_w, V=p.V.copy(), W=p.W.copy(), algo=algo,
+                          levels=L, iters=K))
+    res = h.solve_batch(batch)
+    for (p, algo, L, K), d, (st, sweeps, obj) in zip(probs, batch, res):
+        assert st == 0
+        assert sweeps == sum(native.schedule("vcycle", L, K))
+        V, W = p.V.copy(), p.W.copy()
+        h.solve(p.M, p.grid_h, p.grid_w, V, W, algo, levels=L, iters=K)
+        np.testing.assert_array_equal(d["V"], V)
+        np.testing.assert_array_equal(d["W"], W)
+        assert abs(obj - h.error(p.M, V, W)) <= 1e-9 * obj
+
+
+def test_batch_repeat_and_order_independence(h):
+    probs = _problems(seed0=10)
+    def run(order):
+        batch = [dict(M=probs[i][0].M, grid_h=probs[i][0].grid_h, grid_w=probs[i][0].grid_w, V=probs[i][0].V.copy(),
+                      W=probs[i][0].W.copy(), algo=probs[i][1], levels=probs[i][2], iters=probs[i][3]) for i in order]
+        h.solve_batch(batch)
+        return {i: (d["V"], d["W"]) for i, d in zip(order, batch)}
+    a = run(list(range(len(probs))))
+    b = run(list(reversed(range(len(probs)))))
+    for i in a:
+        np.testing.assert_array_equal(a[i][0], b[i][0])
+        np.testing.assert_array_equal(a[i][1], b[i][1])
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-2])
+def test_stopping_rule_matches_standalone_trace(h, tol):
+    # the batched run stops after the first post-smoothing sweep t with |f_{t-1} - f_t| <= tol f_t
+    p = synth.make_problem(19, 19, 2429, 49, data_seed=3)
+    L, K = 3, 200
+    V, W = p.V.copy(), p.W.copy()
+    n_fine = native.schedule("vcycle", L, K)[0]
+    tr = h.solve(p.M, 19, 19, V, W, "hals", levels=L, iters=K, trace_len=n_fine)
+    post = tr[K // 4:]
+    stop = len(post)
+    for t in range(1, len(post)):
+        if abs(post[t - 1] - post[t]) <= tol * post[t]:
+            stop = t + 1
+            break
+    d = dict(M=p.M, grid_h=19, grid_w=19, V=p.V.copy(), W=p.W.copy(), levels=L, iters=K, rel_tol=tol)
+    (st, sweeps, obj), = h.solve_batch([d])
+    total = sum(native.schedule("vcycle", L, K))
+    assert st == 0
+    assert sweeps == total - len(post) + stop
+    # the iterate is the standalone one after the same number of sweeps
+    V2, W2 = p.V.copy(), p.W.copy()
+    h.solve(p.M, 19, 19, V2, W2, "hals", levels=L, iters=K, stop_after=sweeps)
+    np.testing.assert_array_equal(d["V"], V2)
+    np.testing.assert_array_equal(d["W"], W2)
+    assert abs(obj - post[stop - 1]) <= 1e-12 * obj
+
+
+def test_batch_of_uneven_sizes_against_oracle(h):
+    # a sample of the uneven-size distribution (small enough for the oracle, and with
+    # r <= pixels of the coarsest level, where the iteration is well conditioned), each
+    # result checked against the FP64 oracle within the BF16 floor of 2e-2
+    sizes = [s for s in synth.batched_sizes(64)
+             if s[0] <= 32 and s[1] <= 1200 and s[2] <= ((s[0] + 3) // 4) ** 2][:6]
+    assert len(sizes) >= 3
+    batch, refs = [], []
+    for i, (side, n, r) in enumerate(sizes):
+        p = synth.make_problem(side, side, n, r, data_seed=100 + i)
+        batch.append(dict(M=p.M, grid_h=side, grid_w=side, V=p.V.copy(), W=p.W.copy(), levels=3, iters=12))
+        refs.append(p)
+    res = h.solve_batch(batch)
+    for (st, sweeps, obj), p, d in zip(res, refs, batch):
+        assert st == 0
+        Vo, Wo = o.solve(p.M, p.grid_h, p.grid_w, p.V, p.W, "hals", levels=3, K=12)
+        fo = o.objective(p.M, Vo, Wo)
+        assert abs(obj - fo) <= 2e-2 * fo
+        assert abs(obj - o.objective(p.M, d["V"], d["W"])) <= 1e-6 * obj
