@@ -50,6 +50,11 @@ def parse_args(argv=None):
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-form", action="store_true")
+    ap.add_argument("--no-batched-form", action="store_true")
+    ap.add_argument("--no-serving-form", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--_oracle_sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -389,6 +394,12 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
     out["roofline"], out["kernel_times_per_step_ms"] = roofline(args, h, Md, gh, gw, n, r, sched)
     if not args.no_precision_form:
         out["precision_form"] = precision_form(args)
+    if not (args.no_batched_form and args.no_serving_form):
+        pool = batched_problems(BATCH_COUNT)
+        if not args.no_batched_form:
+            out["batched_form"] = batched_form(args, pool)
+        if not args.no_serving_form:
+            out["serving_form"] = serving_form(args, pool)
     return out
 
 
@@ -514,6 +525,161 @@ def precision_form(args, reps=3):
                 res[label] = entry
         res["oracle_fp64_objective"] = fstar
         out[wl] = res
+    return out
+
+
+# Batched and serving forms: 64 problems of uneven size (side in {16,19,32,64,92,128},
+# n ~ U[200,4000], r ~ U[5,64], data seeds 0..63), multilevel HALS L = 3 with the
+# device-side stopping rule |f_{t-1} - f_t| <= 1e-3 f_t on the finest-level sweeps.
+BATCH_COUNT = 64
+BATCH_LEVELS = 3
+BATCH_ITERS = {"hals": 200, "mu": 200, "anls": 20}
+BATCH_TOL = 1e-3
+
+
+def batched_problems(count):
+    """The seeded uneven-size problems, drawn in parallel in spawned processes."""
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+
+    from paper_1009_0881_gb300 import synth
+
+    sizes = synth.batched_sizes(count)
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(synth.make_problem, side, side, n, r, 0.04 * side if side > 19 else 2.0, i)
+                for i, (side, n, r) in enumerate(sizes)]
+        return [f.result() for f in futs]
+
+
+def _request(p, Md, algo, V=None, W=None):
+    return dict(M=Md, grid_h=p.grid_h, grid_w=p.grid_w, V=p.V.copy() if V is None else V,
+                W=p.W.copy() if W is None else W, algo=algo, levels=BATCH_LEVELS, iters=BATCH_ITERS[algo],
+                rel_tol=BATCH_TOL)
+
+
+def batched_form(args, pool, reps=3):
+    """All 64 problems in one nmf_solve_batch (one CUDA graph of concurrent branches), FP32 and
+    BF16, next to the plain FP32 path solving them one request at a time."""
+    import torch
+
+    from paper_1009_0881_gb300 import native
+
+    stream = torch.cuda.current_stream()
+    Mds = [torch.from_numpy(p.M).cuda() for p in pool]
+    V0s = [torch.from_numpy(p.V).cuda() for p in pool]
+    W0s = [torch.from_numpy(p.W).cuda() for p in pool]
+    Vs = [v.clone() for v in V0s]
+    Ws = [w.clone() for w in W0s]
+    reqs = [_request(p, Md, "hals", V, W) for p, Md, V, W in zip(pool, Mds, Vs, Ws)]
+
+    def reset():
+        for V, W, V0, W0 in zip(Vs, Ws, V0s, W0s):
+            V.copy_(V0)
+            W.copy_(W0)
+
+    out = {"problems": len(pool), "levels": BATCH_LEVELS, "iters_cap": BATCH_ITERS["hals"], "rel_tol": BATCH_TOL,
+           "algo": "hals", "flops_per_batch_note": "sum over problems of the Appendix A.1 sweep cost"}
+    for label, prec, batched in (("batched_fp32", native.NMF_FP32, True), ("batched_bf16", native.NMF_BF16, True),
+                                 ("sequential_plain_fp32", native.NMF_FP32, False)):
+        with native.Handle(0, precision=prec) as hh:
+            hh.set_stream(stream.cuda_stream)
+            ms = []
+            for it in range(1 + reps):
+                reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if batched:
+                    res = hh.solve_batch(reqs)
+                else:
+                    res = [hh.solve_batch([d])[0] for d in reqs]
+                e1.record(stream)
+                e1.synchronize()
+                if it:
+                    ms.append(e0.elapsed_time(e1))
+            t = statistics.median(ms)
+            sweeps = sum(x[1] for x in res)
+            out[label] = {"ms_per_batch": t, "solves_per_s": len(pool) / (t / 1e3), "sweeps": sweeps,
+                          "sweeps_per_s": sweeps / (t / 1e3), "all_ok": all(x[0] == 0 for x in res),
+                          "objective_sum": sum(x[2] for x in res)}
+    out["speedup_batched_bf16_vs_sequential_fp32"] = (out["sequential_plain_fp32"]["ms_per_batch"]
+                                                      / out["batched_bf16"]["ms_per_batch"])
+    out["speedup_batched_fp32_vs_sequential_fp32"] = (out["sequential_plain_fp32"]["ms_per_batch"]
+                                                      / out["batched_fp32"]["ms_per_batch"])
+    del Mds, V0s, W0s, Vs, Ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_form(args, pool):
+    """Poisson arrivals into nmf_server: sizes from the 64-problem pool, algorithm uniform over
+    HALS/MU/ANLS, 40 GB workspace budget.  M stays on the device; each request brings its
+    initial V, W from host memory and gets the result back there."""
+    import numpy as np
+    import torch
+
+    from paper_1009_0881_gb300 import native, synth
+
+    Mds = [torch.from_numpy(p.M).cuda() for p in pool]
+    torch.cuda.synchronize()
+    algos = ("hals", "mu", "anls")
+    budget = 40 * 10**9
+    out = {"rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "slots": args.serve_slots,
+           "hbm_budget_bytes": budget, "levels": BATCH_LEVELS, "iters_cap": BATCH_ITERS, "rel_tol": BATCH_TOL,
+           "sizes": "uniform over the 64 seeded batched-form problems"}
+    n_req = int(args.serve_rate * args.serve_seconds * 1.5) + 16
+    gaps = synth.exponential(7, 11, n_req) / args.serve_rate
+    pick = synth.uniform(7, 12, n_req)
+    for label, prec in (("fp32", native.NMF_FP32), ("bf16", native.NMF_BF16)):
+        with native.Server(0, hbm_budget_bytes=budget, slots=args.serve_slots, precision=prec) as srv:
+            # warm-up: every (problem, algorithm) once, so the slots' graphs and workspaces exist
+            t0 = time.perf_counter()
+            tickets = [srv.submit(_request(p, Md, a)) for p, Md in zip(pool, Mds) for a in algos]
+            warm = [srv.poll(t, -1) for t in tickets]
+            warm_s = time.perf_counter() - t0
+            lat, outstanding, status, by_algo, held = [], {}, [], {a: 0 for a in algos}, 0
+            t_start = time.perf_counter()
+            t_next = t_start
+            i = 0
+            t_end = t_start + args.serve_seconds
+
+            def drain(wait):
+                for t in list(outstanding):
+                    r = srv.poll(t, wait)
+                    if r is not None:
+                        status.append(r[0])
+                        lat.append(r[3])
+                        del outstanding[t]
+
+            while True:
+                now = time.perf_counter()
+                if now >= t_end or i + 1 >= n_req:
+                    break
+                if now >= t_next:
+                    k = min(int(pick[i] * 3 * len(pool)), 3 * len(pool) - 1)
+                    a = algos[k % 3]
+                    p, Md = pool[k // 3], Mds[k // 3]
+                    outstanding[srv.submit(_request(p, Md, a))] = a
+                    by_algo[a] += 1
+                    i += 1
+                    t_next += gaps[i]
+                    continue
+                drain(0)
+                held = max(held, srv.stats()["bytes_held"])
+                time.sleep(min(max(t_next - time.perf_counter(), 0.0), 0.001))
+            submitted = i
+            drain(-1)
+            wall = time.perf_counter() - t_start
+            lat_a = np.array(lat)
+            out[label] = {"submitted": submitted, "completed": len(lat), "all_ok": all(s == 0 for s in status),
+                          "solves_per_s": len(lat) / wall, "wall_s": wall,
+                          "latency_ms": {"p50": float(np.percentile(lat_a, 50)), "p99": float(np.percentile(lat_a, 99)),
+                                         "mean": float(lat_a.mean()), "max": float(lat_a.max())},
+                          "per_algo_requests": by_algo, "max_bytes_held": held, "warmup_s": warm_s,
+                          "warmup_ok": all(w[0] == 0 for w in warm)}
+    del Mds
+    torch.cuda.empty_cache()
     return out
 
 

@@ -148,6 +148,37 @@ typedef struct {
 int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count);
 
 /*
+ * nmf_workspace_bytes - device workspace nmf_solve_batch would hold on h for
+ * the single problem *q (no device work); negative nmf_status on bad input.
+ */
+int64_t nmf_workspace_bytes(nmf_handle h, const nmf_problem* q);
+
+/* nmf_release_workspace - free the handle's device workspace (and its cached graphs). */
+int nmf_release_workspace(nmf_handle h);
+
+/*
+ * Serving form: a request loop with continuous batching.  `slots` worker slots
+ * each own a handle (stream + workspace); a submitted request waits in a FIFO
+ * queue until a slot is free and its workspace fits in the HBM budget
+ * (sum of the workspaces held by all slots <= hbm_budget_bytes; idle slots
+ * release theirs when the queue head does not fit), then runs on that slot's
+ * stream while other requests run on theirs.  Each request is solved exactly
+ * as nmf_solve_batch solves a single problem.
+ */
+typedef struct nmf_server_s* nmf_server;
+int nmf_server_create(nmf_server* out, int device, size_t hbm_budget_bytes, int slots, nmf_precision prec);
+/* Queue *prob (which must stay valid until its ticket completes); returns a ticket >= 0,
+   or NMF_ENOMEM if the problem alone exceeds the budget, NMF_EINVAL on bad input. */
+int64_t nmf_server_submit(nmf_server s, nmf_problem* prob);
+/* NMF_OK once the ticket completed (outputs in its nmf_problem; *latency_ms, if not NULL,
+   receives submit-to-completion time), NMF_EBUSY if not within wait_ms (-1 = wait forever). */
+int nmf_server_poll(nmf_server s, int64_t ticket, int wait_ms, double* latency_ms);
+/* Counters: queued, running, completed requests and device bytes held by the slots. */
+int nmf_server_stats(nmf_server s, int64_t* queued, int64_t* running, int64_t* completed, int64_t* bytes_held);
+/* Waits for queued and running requests, then frees everything. */
+void nmf_server_destroy(nmf_server s);
+
+/*
  * nmf_error - ||M - VW||_F (problem (NMF), Section 2) with float32 products and
  * FP64 accumulation of the squared residuals.  *err_out receives the value
  * (host pointer).

@@ -1135,6 +1135,29 @@ int nmf_solve_ex(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h,
 
 int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count) { return batch_impl(h, probs, count); }
 
+int64_t nmf_workspace_bytes(nmf_handle h, const nmf_problem* q) {
+    if (!h || !q) return NMF_EINVAL;
+    int rc = check_dims(h, q->m, q->n, q->r);
+    if (rc) return rc;
+    if (q->grid_h < 1 || q->grid_w < 1 || (int64_t)q->grid_h * q->grid_w != q->m || q->levels < 1 || q->levels > 16)
+        return fail(h, NMF_EINVAL, "bad problem geometry");
+    std::vector<Plan> plans(1);
+    plan_dims(h, plans[0], q->m, q->n, q->grid_h, q->grid_w, q->r, q->levels, 0);
+    return (int64_t)plans_bytes(h, plans);
+}
+
+int nmf_release_workspace(nmf_handle h) {
+    if (!h) return NMF_EINVAL;
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
+    if (h->ws) CK(cudaFree(h->ws));
+    h->ws = nullptr;
+    h->ws_cap = 0;
+    return NMF_OK;
+}
+
 int nmf_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo, int sweeps, float* V,
               float* W) {
     if (m > (1LL << 31) - 64) return fail(h, NMF_EINVAL, "m too large");

@@ -45,6 +45,14 @@ SIGNATURES = [
     ("nmf_profile_sweep", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
     ("nmf_error_noalloc", _I, [_P, _P, _P, _I64, _I64, _I, _P, ctypes.POINTER(ctypes.c_double)]),
     ("nmf_solve_batch", _I, [_P, _P, _I]),
+    ("nmf_workspace_bytes", _I64, [_P, _P]),
+    ("nmf_release_workspace", _I, [_P]),
+    ("nmf_server_create", _I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I, _I]),
+    ("nmf_server_submit", _I64, [_P, _P]),
+    ("nmf_server_poll", _I, [_P, _I64, _I, ctypes.POINTER(ctypes.c_double)]),
+    ("nmf_server_stats", _I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                              ctypes.POINTER(_I64)]),
+    ("nmf_server_destroy", None, [_P]),
 ]
 
 
@@ -183,25 +191,22 @@ class Handle:
         (status, sweeps_run, objective)."""
         arr = (Problem * len(problems))()
         for q, d in zip(arr, problems):
-            _check_f32(d["M"], d["V"], d["W"])
-            q.M = _ptr(d["M"])
-            q.m, q.n = d["M"].shape
-            q.grid_h, q.grid_w = d["grid_h"], d["grid_w"]
-            q.r = d["V"].shape[1]
-            algo = d.get("algo", "hals")
-            q.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
-            q.levels = d.get("levels", 1)
-            q.iters = d.get("iters", 100)
-            cyc = d.get("cycle", "vcycle")
-            q.cycle = CYCLES[cyc] if isinstance(cyc, str) else int(cyc)
-            q.rel_tol = d.get("rel_tol", 0.0)
-            q.V = _ptr(d["V"])
-            q.W = _ptr(d["W"])
+            fill_problem(q, d)
         rc = self.lib.nmf_solve_batch(self.h, ctypes.cast(arr, _P), len(problems))
         out = [(q.status, q.sweeps_run, q.objective) for q in arr]
         if rc != 0 and all(s == 0 for s, _, _ in out):
             self._rc(rc)
         return out
+
+    def workspace_bytes(self, d: dict) -> int:
+        """nmf_workspace_bytes: device bytes one problem dict needs (nothing is allocated)."""
+        b = int(self.lib.nmf_workspace_bytes(self.h, ctypes.byref(fill_problem(Problem(), d))))
+        if b < 0:
+            self._rc(b)
+        return b
+
+    def release_workspace(self):
+        self._rc(self.lib.nmf_release_workspace(self.h))
 
     def solve_plain(self, M, grid_h, grid_w, V, W, algo="hals", levels=1, iters=100):
         """nmf_solve (V-cycle, no options)."""
@@ -260,6 +265,72 @@ class Handle:
         a = ALGOS[algo] if isinstance(algo, str) else int(algo)
         self._rc(self.lib.nmf_profile_sweep(self.h, _ptr(M), m, n, V.shape[1], a, _ptr(V), _ptr(W), reps, out))
         return list(out)
+
+
+def fill_problem(q: Problem, d: dict) -> Problem:
+    """Marshal a problem dict (M, grid_h, grid_w, V, W, algo, levels, iters, cycle, rel_tol) into q."""
+    _check_f32(d["M"], d["V"], d["W"])
+    q.M = _ptr(d["M"])
+    q.m, q.n = d["M"].shape
+    q.grid_h, q.grid_w = d["grid_h"], d["grid_w"]
+    q.r = d["V"].shape[1]
+    algo = d.get("algo", "hals")
+    q.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    q.levels = d.get("levels", 1)
+    q.iters = d.get("iters", 100)
+    cyc = d.get("cycle", "vcycle")
+    q.cycle = CYCLES[cyc] if isinstance(cyc, str) else int(cyc)
+    q.rel_tol = d.get("rel_tol", 0.0)
+    q.V = _ptr(d["V"])
+    q.W = _ptr(d["W"])
+    return q
+
+
+class Server:
+    """nmf_server: continuous-batching request loop (native threads, one stream per slot)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, slots: int = 4, precision: int = NMF_FP32):
+        self.lib = load()
+        s = _P()
+        rc = self.lib.nmf_server_create(ctypes.byref(s), device, hbm_budget_bytes, slots, precision)
+        if rc != 0:
+            raise NMFError(rc, "nmf_server_create failed")
+        self.s = s
+        self._keep = {}
+
+    def submit(self, d: dict) -> int:
+        """Queue a problem dict; the arrays in it must stay alive until the ticket completes."""
+        q = fill_problem(Problem(), d)
+        t = int(self.lib.nmf_server_submit(self.s, ctypes.byref(q)))
+        if t < 0:
+            raise NMFError(t, "nmf_server_submit failed")
+        self._keep[t] = (q, d)
+        return t
+
+    def poll(self, ticket: int, wait_ms: int = -1):
+        """Returns None while running, else (status, sweeps_run, objective, latency_ms)."""
+        lat = ctypes.c_double(0.0)
+        rc = self.lib.nmf_server_poll(self.s, ticket, wait_ms, ctypes.byref(lat))
+        if rc == -6:
+            return None
+        q, _ = self._keep.pop(ticket)
+        return rc, q.sweeps_run, q.objective, lat.value
+
+    def stats(self):
+        v = [_I64(0) for _ in range(4)]
+        self.lib.nmf_server_stats(self.s, *[ctypes.byref(x) for x in v])
+        return dict(zip(("queued", "running", "completed", "bytes_held"), (x.value for x in v)))
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.nmf_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def error_noalloc(M, V, W, stream_ptr: int | None = None) -> float:

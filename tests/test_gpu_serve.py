@@ -1,0 +1,125 @@
+"""GPU tests of the serving form (nmf_server_*): requests of uneven size arrive
+while others run; native worker threads, one stream and workspace per slot,
+admit them in arrival order under an HBM budget.
+
+Required properties: a request's result is bitwise the one nmf_solve_batch
+gives it alone (same plan, same kernels, same summation orders); the memory the
+slots hold never exceeds the budget; a request larger than the budget is
+refused at submission with NMF_ENOMEM.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1009_0881_gb300 import native, synth
+
+pytestmark = pytest.mark.gpu
+
+REQS = [  # (side_h, side_w, n, r, algo, levels, iters)
+    (16, 16, 700, 10, "hals", 3, 40),
+    (32, 32, 300, 5, "mu", 3, 40),
+    (19, 19, 2429, 49, "anls", 2, 4),
+    (64, 64, 1200, 64, "hals", 2, 12),
+    (92, 92, 250, 23, "mu", 3, 16),
+    (16, 16, 900, 7, "hals", 1, 30),
+    (128, 128, 400, 33, "hals", 3, 8),
+    (24, 24, 500, 12, "anls", 3, 6),
+]
+
+
+@pytest.fixture(scope="module", params=[native.NMF_FP32, native.NMF_BF16], ids=["fp32", "bf16"])
+def ref(request):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1009_0881_gb300 import build
+    build.build()
+    with native.Handle(0, precision=request.param) as hd:
+        hd.precision = request.param
+        yield hd
+
+
+def _requests(seed0):
+    out = []
+    for i, (gh, gw, n, r, algo, L, K) in enumerate(REQS):
+        p = synth.make_problem(gh, gw, n, r, sigma=0.04 * gw if gw > 19 else 2.0, data_seed=seed0 + i)
+        out.append(dict(M=p.M, grid_h=gh, grid_w=gw, V=p.V.copy(), W=p.W.copy(), algo=algo, levels=L, iters=K))
+    return out
+
+
+def _alone(ref, reqs):
+    res = []
+    for d in reqs:
+        e = dict(d, V=d["V"].copy(), W=d["W"].copy())
+        (st, sweeps, obj), = ref.solve_batch([e])
+        assert st == 0
+        res.append((e["V"], e["W"], sweeps, obj))
+    return res
+
+
+def _serve(srv, reqs, gap_s=0.0):
+    tickets = []
+    for d in reqs:
+        tickets.append(srv.submit(d))
+        if gap_s:
+            time.sleep(gap_s)
+    return [srv.poll(t, -1) for t in tickets]
+
+
+def test_served_equals_alone(ref):
+    reqs = _requests(200)
+    want = _alone(ref, reqs)
+    with native.Server(0, slots=3, precision=ref.precision) as srv:
+        got = _serve(srv, reqs, gap_s=0.002)
+        assert srv.stats()["completed"] == len(reqs)
+    for d, (V, W, sweeps, obj), (st, sw, ob, lat) in zip(reqs, want, got):
+        assert st == 0 and lat > 0
+        assert sw == sweeps
+        np.testing.assert_array_equal(d["V"], V)
+        np.testing.assert_array_equal(d["W"], W)
+        assert ob == obj
+
+
+def test_budget_admission(ref):
+    reqs = _requests(300)
+    want = _alone(ref, reqs)
+    need = [ref.workspace_bytes(d) for d in reqs]
+    # room for the largest request and a little more: slots must give memory back
+    budget = max(need) + min(need)
+    seen = []
+    stop = threading.Event()
+    with native.Server(0, hbm_budget_bytes=budget, slots=4, precision=ref.precision) as srv:
+        def watch():
+            while not stop.is_set():
+                seen.append(srv.stats()["bytes_held"])
+                time.sleep(0.0005)
+        th = threading.Thread(target=watch)
+        th.start()
+        try:
+            got = _serve(srv, reqs)
+        finally:
+            stop.set()
+            th.join()
+        # a request larger than the budget is refused up front
+        big = synth.make_problem(128, 128, 4000, 64, data_seed=1)
+        d = dict(M=big.M, grid_h=128, grid_w=128, V=big.V.copy(), W=big.W.copy(), levels=3, iters=4)
+        assert ref.workspace_bytes(d) > budget
+        with pytest.raises(native.NMFError) as ei:
+            srv.submit(d)
+        assert ei.value.code == -2
+    assert max(seen) <= budget
+    for d, (V, W, sweeps, obj), (st, sw, ob, lat) in zip(reqs, want, got):
+        assert st == 0
+        np.testing.assert_array_equal(d["V"], V)
+        np.testing.assert_array_equal(d["W"], W)
+
+
+def test_bad_request_fails_alone(ref):
+    reqs = _requests(400)[:3]
+    bad = dict(reqs[1], levels=0)
+    with native.Server(0, slots=2, precision=ref.precision) as srv:
+        with pytest.raises(native.NMFError):
+            srv.submit(bad)
+        got = _serve(srv, reqs)
+    assert all(g[0] == 0 for g in got)
