@@ -175,7 +175,7 @@ def main_ours(args):
     import numpy as np
     import torch
 
-    from paper_1009_0881_gb300 import native, synth
+    from paper_1009_0881_gb300 import native, replicas, synth
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -198,7 +198,7 @@ def main_ours(args):
     build.build()
     gh, gw, n, r, sigma = synth.WORKLOADS[args.workload]
     # independent problem per rank (replicas): weak scaling
-    prob = synth.make_problem(gh, gw, n, r, sigma=sigma, data_seed=1 + rank)
+    prob = synth.make_problem(gh, gw, n, r, sigma=sigma, data_seed=replicas.replica_seed(rank))
     m = gh * gw
     sched = native.schedule("vcycle", args.levels, args.iters)
     sweeps_per_step = sum(sched)
@@ -250,12 +250,8 @@ def main_ours(args):
         torch.distributed.barrier()
     total_ms = sum(times)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = replicas.aggregate_throughput(sweeps_per_step * args.steps, total_ms, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * sweeps_per_step * args.steps / (total_ms / 1e3)
 
     # --- e2e through nmf_solve on pinned host buffers -----------------------
     Mh = torch.from_numpy(prob.M).pin_memory()
@@ -403,6 +399,31 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
     return out
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture,
+# valid while the kernel's sources hash to `src`; the captures and their commands are
+# summarised under profiles/.
+TRAFFIC = {
+    "half_sweep_kernel": {"bytes": 0.5 * (4.581888e6 + 4.233216e6), "src": "f9a05243749f2b37",
+                          "files": ("fused.cu", "fused.cuh", "rowupdate.cuh", "ptx.cuh", "nmf_internal.cuh"),
+                          "scope": "mean of the finest-level V-step and W-step launches, 19x19 grid n=2429 r=49"},
+    "tc_gemm_kernel": {"bytes": 262.546176e6 + 13.465856e6, "src": "48475781f0146f45",
+                       "files": ("tc_gemm.cu", "tc_gemm.cuh", "ptx.cuh", "nmf_internal.cuh"),
+                       "scope": "finest-level V-step product, 256x256 grid n=2000 r=64"},
+}
+
+
+def _traffic(kernel):
+    """Captured DRAM bytes per launch, or None if the kernel changed since the capture."""
+    import hashlib
+
+    t = TRAFFIC[kernel]
+    hsh = hashlib.sha256()
+    for f in t["files"]:
+        with open(os.path.join(ROOT, "paper_1009_0881_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return t["bytes"] if hsh.hexdigest()[:16] == t["src"] else None
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -455,7 +476,8 @@ def roofline(args, h, Md, gh, gw, n, r, sched):
     achieved = flops / (ms / 1e3) / 1e12
     peak = fp32_peak / 1e12
     roof = {"kernel": hs, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "launches_per_step": launches,
+            "frac": achieved / peak, "traffic": _traffic("half_sweep_kernel"),
+            "traffic_scope": TRAFFIC["half_sweep_kernel"]["scope"], "launches_per_step": launches,
             "mean_launch_us": 1e3 * ms / launches,
             "peak_basis": f"FP32 FFMA: {n_sms} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (derived)"}
     return roof, times
@@ -520,7 +542,7 @@ def precision_form(args, reps=3):
                                           "gram+rows W": tt[3]}
                     entry["roofline"] = {"kernel": "tc_gemm_kernel (V-step, A = M W^T, finest level)",
                                          "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                                         "frac": ach / hbm, "traffic": None,
+                                         "frac": ach / hbm, "traffic": _traffic("tc_gemm_kernel"),
                                          "algorithmic_bytes": bytes_v}
                 res[label] = entry
         res["oracle_fp64_objective"] = fstar

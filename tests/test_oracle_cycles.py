@@ -45,6 +45,28 @@ def test_nested_iteration_sweep_allocation_matches_table1(row):
     assert _count_sweeps("ni", L, 4 * k) == row[2:]
 
 
+def _level_sequence(cycle, L, K, h=16, w=16):
+    """Levels of the sweeps in the order a cycle runs them."""
+    p = synth.make_problem(h, w, 4, 2, data_seed=1)
+    trace = []
+    orig = dict(o.SWEEPS)
+    o.SWEEPS["count"] = lambda M, V, W: (V, W)
+    try:
+        o.solve(p.M, h, w, p.V, p.W, algo="count", levels=L, K=K, cycle=cycle, trace=trace)
+    finally:
+        o.SWEEPS.clear()
+        o.SWEEPS.update(orig)
+    return [level for level, _ in trace]
+
+
+def test_vcycle_order_follows_algorithm():
+    # Algorithm V-cycle: pre-smoothing at the fine level, the coarse cycle, then post-smoothing
+    K = 8
+    assert _level_sequence("vcycle", 2, K) == [1] * (K // 4) + [2] * K + [1] * (K // 2)
+    assert _level_sequence("vcycle", 3, K) == ([1] * (K // 4) + [2] * (K // 4) + [3] * K + [2] * (K // 2)
+                                               + [1] * (K // 2))
+
+
 def test_fmg_allocation():
     # FMG(L, K) = FMG(L-1, K) on the coarser level, then V-cycle(L, 3K/4)
     K = 400

@@ -1,0 +1,154 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in the oracle (monkeypatching a function of
+oracle/nmf_oracle.py, on the CPU) and runs the pin tests that should notice it;
+at least one of them must fail.  The unpatched oracle passes all of them
+(the same tests run unpatched in the other test modules).
+"""
+import numpy as np
+import pytest
+
+import test_oracle_cycles as tc
+import test_oracle_sweeps as ts
+import test_oracle_transfer as tt
+from oracle import nmf_oracle as o
+
+
+def _fails(*checks):
+    """True if at least one check raises AssertionError."""
+    for chk in checks:
+        try:
+            chk()
+        except AssertionError:
+            return True
+    return False
+
+
+def _hals_col_drop_term(V, A, B, k):
+    # dropped term: forgets the coupling to the other columns
+    if B[k, k] <= 0.0:
+        return
+    V[:, k] = np.maximum(0.0, A[:, k] / B[k, k])
+
+
+def _hals_col_wrong_sign(V, A, B, k):
+    if B[k, k] <= 0.0:
+        return
+    others = [l for l in range(V.shape[1]) if l != k]
+    V[:, k] = np.maximum(0.0, (A[:, k] + V[:, others] @ B[others, k]) / B[k, k])
+
+
+def _hals_row_wrong_index(W, C, D, k):
+    # wrong index: divides by the first diagonal entry of D instead of D_kk
+    if D[k, k] <= 0.0:
+        return
+    others = [l for l in range(W.shape[0]) if l != k]
+    W[k, :] = np.maximum(0.0, (C[k, :] - D[k, others] @ W[others, :]) / D[0, 0])
+
+
+def _hals_no_clamp(V, A, B, k):
+    if B[k, k] <= 0.0:
+        return
+    others = [l for l in range(V.shape[1]) if l != k]
+    V[:, k] = (A[:, k] - V[:, others] @ B[others, k]) / B[k, k]
+
+
+def _mu_old_v(M, V, W):
+    # W-step with the old V (Jacobi instead of the algorithm's order)
+    V = np.array(V, dtype=np.float64)
+    W = np.array(W, dtype=np.float64)
+    Vn = V * (M @ W.T) / np.maximum(V @ (W @ W.T), o.EPS_MU)
+    Wn = W * (V.T @ M) / np.maximum((V.T @ V) @ W, o.EPS_MU)
+    return Vn, Wn
+
+
+def _mu_transposed(M, V, W):
+    V = np.array(V, dtype=np.float64)
+    W = np.array(W, dtype=np.float64)
+    V = V * (M @ W.T) / np.maximum(V @ (W @ W.T), o.EPS_MU)
+    W = W * (V.T @ M) / np.maximum((V @ V.T)[: V.shape[1], : V.shape[1]] @ W, o.EPS_MU)
+    return V, W
+
+
+def _nnls_clip(G, b, max_outer=None):
+    # projection of the unconstrained solution instead of the active-set method
+    return np.maximum(0.0, np.linalg.solve(G + 1e-12 * np.eye(len(b)), b))
+
+
+def _objective_squared(M, V, W):
+    R = np.asarray(M, dtype=np.float64) - np.asarray(V, dtype=np.float64) @ np.asarray(W, dtype=np.float64)
+    return float((R * R).sum())
+
+
+def _rd_half_floor(k):
+    return (k // 2,)
+
+
+def _weight_corner_2(dy, dx):
+    return 2.0 if (dy and dx) else float((2 - abs(dy)) * (2 - abs(dx)))
+
+
+def _weight_flat(dy, dx):
+    return 1.0
+
+
+def _vcycle_swapped_budget(Ms, grids, V, W, algo, L, K, level=0, hooks=None, trace=None):
+    M = Ms[level]
+    if L == 1:
+        return o.smooth(M, V, W, algo, K, trace, level + 1)
+    V, W = o.smooth(M, V, W, algo, K // 2, trace, level + 1)
+    Vc = o.restrict(V, *grids[level])
+    Vc, W = _vcycle_swapped_budget(Ms, grids, Vc, W, algo, L - 1, K, level + 1, hooks, trace)
+    V = o.prolong(Vc, *grids[level + 1], *grids[level])
+    return o.smooth(M, V, W, algo, K // 4, trace, level + 1)
+
+
+def _vcycle_coarsest_half(Ms, grids, V, W, algo, L, K, level=0, hooks=None, trace=None):
+    M = Ms[level]
+    if L == 1:
+        return o.smooth(M, V, W, algo, K // 2, trace, level + 1)
+    V, W = o.smooth(M, V, W, algo, K // 4, trace, level + 1)
+    Vc = o.restrict(V, *grids[level])
+    Vc, W = _vcycle_coarsest_half(Ms, grids, Vc, W, algo, L - 1, K, level + 1, hooks, trace)
+    V = o.prolong(Vc, *grids[level + 1], *grids[level])
+    return o.smooth(M, V, W, algo, K // 2, trace, level + 1)
+
+
+def _table1_checks():
+    return [lambda row=row: tc.test_vcycle_sweep_allocation_matches_table1(row) for row in tc._table1_rows()]
+
+
+MUTANTS = {
+    "restriction corner weight 2": ("restriction_weight", _weight_corner_2,
+                                    [tt.test_restriction_matches_printed_3x3_example,
+                                     tt.test_interior_restriction_is_eq_4_1]),
+    "restriction unweighted": ("restriction_weight", _weight_flat,
+                               [tt.test_restriction_matches_printed_3x3_example]),
+    "prolongation drops odd neighbour": ("rd_half", _rd_half_floor,
+                                         [tt.test_prolongation_matches_printed_2x2_example]),
+    "HALS dropped coupling term": ("hals_update_V_column", _hals_col_drop_term,
+                                   [lambda: ts.test_hals_column_update_is_exact_1d_minimiser(0)]),
+    "HALS wrong sign": ("hals_update_V_column", _hals_col_wrong_sign,
+                        [lambda: ts.test_hals_column_update_is_exact_1d_minimiser(0)]),
+    "HALS missing clamp": ("hals_update_V_column", _hals_no_clamp,
+                           [ts.test_hals_clamp_produces_zeros,
+                            lambda: ts.test_hals_column_update_is_exact_1d_minimiser(0)]),
+    "HALS W-row wrong diagonal index": ("hals_update_W_row", _hals_row_wrong_index,
+                                        [lambda: ts.test_hals_row_update_is_exact_1d_minimiser(0)]),
+    "MU W-step with old V": ("mu_sweep", _mu_old_v, [ts.test_mu_elementwise_formula_by_loops]),
+    "MU transposed Gram": ("mu_sweep", _mu_transposed, [ts.test_mu_elementwise_formula_by_loops]),
+    "NNLS clipped least squares": ("nnls_active_set", _nnls_clip,
+                                   [lambda: ts.test_nnls_equals_support_enumeration(s) for s in range(8)]),
+    "objective squared": ("objective", _objective_squared, [ts.test_objective_is_frobenius_norm_by_loops]),
+    "V-cycle pre/post budgets swapped": ("vcycle", _vcycle_swapped_budget, [tc.test_vcycle_order_follows_algorithm]),
+    "V-cycle coarsest level short": ("vcycle", _vcycle_coarsest_half, _table1_checks()),
+}
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_pins_catch_planted_mistake(name, monkeypatch):
+    attr, bad, checks = MUTANTS[name]
+    monkeypatch.setattr(o, attr, bad)
+    if attr == "mu_sweep":
+        monkeypatch.setitem(o.SWEEPS, "mu", bad)
+    assert _fails(*checks), f"no pin noticed: {name}"
