@@ -18,7 +18,6 @@ namespace nmfk {
 namespace {
 
 using rowupd::f4add;
-using rowupd::update_rows;
 constexpr int NT = rowupd::NT;
 constexpr int BA = 64;
 
@@ -104,17 +103,9 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
 
     if (MODE != rowupd::kModeStore) {
         for (int k = tid; k < kMaxRank; k += NT) Ginv[k] = (k < r && Gs[k * rp + k] > 0.f) ? 1.f / Gs[k * rp + k] : 0.f;
-        for (int e = tid; e < R * kMaxRank; e += NT) {
-            const int rr = e / kMaxRank, k = e - rr * kMaxRank;
-            float s = 0.f;
-            if (k < r) {
-                const float* fr = Fn + rr * kMaxRank;
-                for (int l = 0; l < r; ++l) s = fmaf(fr[l], Gs[l * rp + k], s);
-            }
-            Dn[e] = s;
-        }
+        rowupd::rows_times_gram<4>(R, r, rp, Fn, Gs, Dn);
         __syncthreads();
-        update_rows<8, MODE>(q.F, (int)q.rows, r, rp, R, row0, Fn, Ared, Dn, Gs, Ginv);
+        rowupd::update_rows_any<MODE>(q.F, (int)q.rows, r, rp, R, row0, Fn, Ared, Dn, Gs, Ginv);
         __syncthreads();
     } else {
         // rows past the end read as zero already; nothing to update
@@ -137,6 +128,7 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) ga[i][j] = 0.f;
+#pragma unroll 4
         for (int rr = 0; rr < R; ++rr) {
             const float4 u = *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + ty * 4);
             const float4 v = *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + tx * 4);

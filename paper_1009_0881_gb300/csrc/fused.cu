@@ -45,14 +45,14 @@ namespace {
 
 using rowupd::cluster_sum_f4;
 using rowupd::f4add;
-using rowupd::update_rows;
 
-constexpr int BA = 64;    // tile rows
 constexpr int KS = 32;    // K rows per pipeline stage
 constexpr int NST = 4;    // pipeline stages
 constexpr int NT = 256;   // threads
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kStageF4 = 1920;  // float4 slots staging the Gram slabs of this CTA's slice
+// float4 slots staging the Gram slabs of this CTA's slice (smaller for cs = 1, where
+// the slice is the whole matrix and the layout would not fit the 227 KiB limit)
+__host__ __device__ inline int stage_f4(int cs) { return cs >= 2 ? 3072 : 1920; }
 
 struct Smem {
     // byte offsets inside the dynamic shared-memory block
@@ -65,7 +65,7 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 __host__ __device__ inline int slab_f4(int r, int rp) { return r * rp / 4; }
 __host__ __device__ inline int slice_f4(int r, int rp, int cs) { return (slab_f4(r, rp) + cs - 1) / cs; }
 
-__host__ __device__ inline Smem smem_layout(int br, int r, int rp, int cs) {
+__host__ __device__ inline Smem smem_layout(int br, int BA, int r, int rp, int cs) {
     Smem s{};
     size_t o = 0;
     const int R = BA / cs;
@@ -75,7 +75,7 @@ __host__ __device__ inline Smem smem_layout(int br, int r, int rp, int cs) {
     s.pt = o;   o = align_up(o + sizeof(float) * BA * br, 128);
     s.gsl = o;  o = align_up(o + sizeof(float4) * S4, 128);
     s.part = o; o = align_up(o + sizeof(float4) * NT, 128);
-    s.gst = o;  o = align_up(o + sizeof(float4) * kStageF4, 128);
+    s.gst = o;  o = align_up(o + sizeof(float4) * stage_f4(cs), 128);
     s.gs = o;   o = align_up(o + sizeof(float) * r * rp, 128);
     s.ginv = o; o = align_up(o + sizeof(float) * kMaxRank, 128);
     s.ared = o; o = align_up(o + sizeof(float) * R * kMaxRank, 128);
@@ -87,11 +87,11 @@ __host__ __device__ inline Smem smem_layout(int br, int r, int rp, int cs) {
     return s;
 }
 
-template <int BR, int MODE>
+template <int BR, int BA, int MODE>
 __global__ void __launch_bounds__(NT, 1)
     half_sweep_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                       const HalfSweepParams p) {
-    constexpr int TM = 4;
+    constexpr int TM = BA / 16;
     constexpr int TN = BR / 16;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(NT, 1)
     const int R = BA / cs;
     const int F4 = slab_f4(r, rp);
     const int S4 = slice_f4(r, rp, cs);
-    const Smem L = smem_layout(BR, r, rp, cs);
+    const Smem L = smem_layout(BR, BA, r, rp, cs);
     float* Xs = reinterpret_cast<float*>(smem_raw + L.xs);
     float* Ys = reinterpret_cast<float*>(smem_raw + L.ys);
     float* Pt = reinterpret_cast<float*>(smem_raw + L.pt);
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NT, 1)
     // When the slice of every slab fits the staging area it is copied
     // asynchronously now and summed after the main loop; otherwise it is summed
     // here, slabs split over NG thread groups, groups combined in a fixed order.
-    const bool staged = S4 * p.gin_count <= kStageF4;
+    const bool staged = S4 * p.gin_count <= stage_f4(cs);
     if (staged) {
         const float4* gin = reinterpret_cast<const float4*>(p.Gin);
         const int64_t gstride4 = p.gin_stride / 4;
@@ -225,8 +225,20 @@ __global__ void __launch_bounds__(NT, 1)
         const float* ys = Ys + slot * KS * BR;
 #pragma unroll 8
         for (int kk = 0; kk < KS; ++kk) {
-            const float4 a4 = *reinterpret_cast<const float4*>(xs + kk * BA + ty * TM);
-            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+            float av[TM];
+            if (TM == 4) {
+                const float4 a4 = *reinterpret_cast<const float4*>(xs + kk * BA + ty * TM);
+                av[0] = a4.x;
+                av[1 % TM] = a4.y;
+                av[2 % TM] = a4.z;
+                av[3 % TM] = a4.w;
+            } else if (TM == 2) {
+                const float2 a2 = *reinterpret_cast<const float2*>(xs + kk * BA + ty * TM);
+                av[0] = a2.x;
+                av[1 % TM] = a2.y;
+            } else {
+                av[0] = xs[kk * BA + ty];
+            }
             float bv[TN];
             if (TN == 4) {
                 const float4 b4 = *reinterpret_cast<const float4*>(ys + kk * BR + tx * TN);
@@ -299,25 +311,10 @@ __global__ void __launch_bounds__(NT, 1)
             if (row < p.Na) p.Pout[row * rp + k] = Ared[rr * kMaxRank + k];
         }
     } else {
-        // d = F_i G for the incoming rows (all threads; one output per thread and pass)
-        for (int e = tid; e < R * kMaxRank; e += NT) {
-            const int rr = e / kMaxRank, k = e - rr * kMaxRank;
-            float s = 0.f;
-            if (k < r) {
-                const float* fr = Fn + rr * kMaxRank;
-                for (int l = 0; l < r; ++l) s = fmaf(fr[l], Gs[l * rp + k], s);
-            }
-            Dn[e] = s;
-        }
+        // d = F_i G for the incoming rows
+        rowupd::rows_times_gram_any(R, r, rp, Fn, Gs, Dn);
         __syncthreads();
-        const int64_t rowbase = (int64_t)a0 + row0;
-        const int rpw = R <= 8 ? 1 : (R <= 16 ? 2 : (R <= 32 ? 4 : 8));
-        switch (rpw) {
-            case 1: update_rows<1, MODE>(p.F, p.Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
-            case 2: update_rows<2, MODE>(p.F, p.Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
-            case 4: update_rows<4, MODE>(p.F, p.Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
-            default: update_rows<8, MODE>(p.F, p.Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
-        }
+        rowupd::update_rows_any<MODE>(p.F, p.Na, r, rp, R, (int64_t)a0 + row0, Fn, Ared, Dn, Gs, Ginv);
         __syncthreads();
         // partial Gram of this CTA's new rows, 4 x 4 outputs per thread (rows past Na are zero)
         {
@@ -326,6 +323,7 @@ __global__ void __launch_bounds__(NT, 1)
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) ga[i][j] = 0.f;
+#pragma unroll 4
             for (int rr = 0; rr < R; ++rr) {
                 const float4 u = *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + ty * 4);
                 const float4 v = *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + tx * 4);
@@ -360,12 +358,12 @@ __global__ void __launch_bounds__(NT, 1)
     cluster.sync();  // #4: keep this CTA's shared memory alive until all remote reads are done
 }
 
-// Partial Gram slabs of a tall factor: out[t] = F[64t:64t+64]^T F[64t:64t+64].
+// Partial Gram slabs of a tall factor: out[t] = F[bt t : bt t + bt]^T F[bt t : bt t + bt], bt <= 64.
 __global__ void __launch_bounds__(256) gram_tiles_kernel(const float* __restrict__ F, int64_t rows, int r, int rp,
-                                                         float* __restrict__ out, int64_t out_stride) {
-    __shared__ float Fs[BA][kMaxRank + 1];
-    const int64_t r0 = (int64_t)blockIdx.x * BA;
-    for (int e = threadIdx.x; e < BA * rp; e += blockDim.x) {
+                                                         int bt, float* __restrict__ out, int64_t out_stride) {
+    __shared__ float Fs[64][kMaxRank + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * bt;
+    for (int e = threadIdx.x; e < bt * rp; e += blockDim.x) {
         const int rr = e / rp, k = e - rr * rp;
         Fs[rr][k] = (r0 + rr < rows) ? F[(r0 + rr) * rp + k] : 0.f;
     }
@@ -374,15 +372,15 @@ __global__ void __launch_bounds__(256) gram_tiles_kernel(const float* __restrict
     for (int idx = threadIdx.x; idx < r * rp; idx += blockDim.x) {
         const int l = idx / rp, k = idx - l * rp;
         float s = 0.f;
-        for (int rr = 0; rr < BA; ++rr) s = fmaf(Fs[rr][l], Fs[rr][k], s);
+        for (int rr = 0; rr < bt; ++rr) s = fmaf(Fs[rr][l], Fs[rr][k], s);
         o[(int64_t)l * rp + k] = s;
     }
 }
 
-template <int BR, int MODE>
+template <int BR, int BA, int MODE>
 cudaError_t launch_t(const HalfSweepLaunch& hl, cudaStream_t st) {
-    const Smem L = smem_layout(BR, hl.p.r, hl.p.rp, hl.p.cs);
-    auto kern = half_sweep_kernel<BR, MODE>;
+    const Smem L = smem_layout(BR, BA, hl.p.r, hl.p.rp, hl.p.cs);
+    auto kern = half_sweep_kernel<BR, BA, MODE>;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)(hl.tiles * hl.p.cs));
     cfg.blockDim = dim3(NT);
@@ -402,13 +400,14 @@ cudaError_t launch_t(const HalfSweepLaunch& hl, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, kern, hl.tmX, hl.tmY, hl.p);
 }
 
-template <int BR>
+template <int BR, int BA>
 cudaError_t set_attrs_br() {
     size_t maxs = 0;
-    for (int cs = 1; cs <= 16; cs *= 2) maxs = std::max(maxs, smem_layout(BR, kMaxRank, kMaxRank, cs).total);
+    for (int cs = 1; cs <= 16; cs *= 2) maxs = std::max(maxs, smem_layout(BR, BA, kMaxRank, kMaxRank, cs).total);
     if (maxs > 232448) return cudaErrorInvalidConfiguration;  // 227 KiB opt-in limit per block
-    const void* ks[3] = {(const void*)half_sweep_kernel<BR, kModeHals>, (const void*)half_sweep_kernel<BR, kModeMu>,
-                         (const void*)half_sweep_kernel<BR, kModeStore>};
+    const void* ks[3] = {(const void*)half_sweep_kernel<BR, BA, kModeHals>,
+                         (const void*)half_sweep_kernel<BR, BA, kModeMu>,
+                         (const void*)half_sweep_kernel<BR, BA, kModeStore>};
     for (const void* k : ks) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxs);
         if (e != cudaSuccess) return e;
@@ -418,67 +417,100 @@ cudaError_t set_attrs_br() {
     return cudaSuccess;
 }
 
+template <int BA>
+const void* hals_kernel_ptr(int br) {
+    switch (br) {
+        case 16: return (const void*)half_sweep_kernel<16, BA, kModeHals>;
+        case 32: return (const void*)half_sweep_kernel<32, BA, kModeHals>;
+        case 48: return (const void*)half_sweep_kernel<48, BA, kModeHals>;
+        default: return (const void*)half_sweep_kernel<64, BA, kModeHals>;
+    }
+}
+
 }  // namespace
 
-size_t half_sweep_smem_bytes(int br, int r, int cs) { return smem_layout(br, r, (int)round_up(r, 4), cs).total; }
+size_t half_sweep_smem_bytes(int br, int ba, int r, int cs) {
+    return smem_layout(br, ba, r, (int)round_up(r, 4), cs).total;
+}
 
 cudaError_t half_sweep_init() {
-    cudaError_t e = set_attrs_br<16>();
-    if (e == cudaSuccess) e = set_attrs_br<32>();
-    if (e == cudaSuccess) e = set_attrs_br<48>();
-    if (e == cudaSuccess) e = set_attrs_br<64>();
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = set_attrs_br<16, 64>();
+    if (e == cudaSuccess) e = set_attrs_br<32, 64>();
+    if (e == cudaSuccess) e = set_attrs_br<48, 64>();
+    if (e == cudaSuccess) e = set_attrs_br<64, 64>();
+    if (e == cudaSuccess) e = set_attrs_br<16, 32>();
+    if (e == cudaSuccess) e = set_attrs_br<32, 32>();
+    if (e == cudaSuccess) e = set_attrs_br<48, 32>();
+    if (e == cudaSuccess) e = set_attrs_br<64, 32>();
+    if (e == cudaSuccess) e = set_attrs_br<16, 16>();
+    if (e == cudaSuccess) e = set_attrs_br<32, 16>();
+    if (e == cudaSuccess) e = set_attrs_br<48, 16>();
+    if (e == cudaSuccess) e = set_attrs_br<64, 16>();
     return e;
 }
 
-int half_sweep_active_clusters(int br, int r, int cs) {
+int half_sweep_active_clusters(int br, int ba, int r, int cs) {
     // how many clusters of `cs` CTAs the device can hold at once with this kernel's shared memory
-    {
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(cs);
-        cfg.blockDim = dim3(NT);
-        cfg.dynamicSmemBytes = smem_layout(br, r, (int)round_up(r, 4), cs).total;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cs;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int n = 0;
-        const void* k = nullptr;
-        switch (br) {
-            case 16: k = (const void*)half_sweep_kernel<16, kModeHals>; break;
-            case 32: k = (const void*)half_sweep_kernel<32, kModeHals>; break;
-            case 48: k = (const void*)half_sweep_kernel<48, kModeHals>; break;
-            default: k = (const void*)half_sweep_kernel<64, kModeHals>; break;
-        }
-        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess) return n;
-        cudaGetLastError();
-    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem_layout(br, ba, r, (int)round_up(r, 4), cs).total;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const void* k = ba == 16 ? hals_kernel_ptr<16>(br) : (ba == 32 ? hals_kernel_ptr<32>(br) : hals_kernel_ptr<64>(br));
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess) return n;
+    cudaGetLastError();
     return 0;
 }
 
 cudaError_t half_sweep_launch(const HalfSweepLaunch& hl, cudaStream_t st) {
-#define NMF_HS_CASE(BRV)                                                      \
-    case BRV:                                                                 \
-        if (hl.mode == kModeHals) return launch_t<BRV, kModeHals>(hl, st);    \
-        if (hl.mode == kModeMu) return launch_t<BRV, kModeMu>(hl, st);        \
-        return launch_t<BRV, kModeStore>(hl, st);
+#define NMF_HS_CASE(BRV, BAV)                                                      \
+    case BRV:                                                                      \
+        if (hl.mode == kModeHals) return launch_t<BRV, BAV, kModeHals>(hl, st);    \
+        if (hl.mode == kModeMu) return launch_t<BRV, BAV, kModeMu>(hl, st);        \
+        return launch_t<BRV, BAV, kModeStore>(hl, st);
+    if (hl.ba == 16) {
+        switch (hl.br) {
+            NMF_HS_CASE(16, 16)
+            NMF_HS_CASE(32, 16)
+            NMF_HS_CASE(48, 16)
+            NMF_HS_CASE(64, 16)
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (hl.ba == 32) {
+        switch (hl.br) {
+            NMF_HS_CASE(16, 32)
+            NMF_HS_CASE(32, 32)
+            NMF_HS_CASE(48, 32)
+            NMF_HS_CASE(64, 32)
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (hl.ba != 64) return cudaErrorInvalidValue;
     switch (hl.br) {
-        NMF_HS_CASE(16)
-        NMF_HS_CASE(32)
-        NMF_HS_CASE(48)
-        NMF_HS_CASE(64)
+        NMF_HS_CASE(16, 64)
+        NMF_HS_CASE(32, 64)
+        NMF_HS_CASE(48, 64)
+        NMF_HS_CASE(64, 64)
         default: return cudaErrorInvalidValue;
     }
 #undef NMF_HS_CASE
 }
 
-cudaError_t gram_tiles_launch(const float* F, int64_t rows, int r, int rp, float* out, int64_t out_stride,
-                              cudaStream_t st) {
-    const int64_t tiles = (rows + BA - 1) / BA;
+cudaError_t gram_tiles_launch(const float* F, int64_t rows, int r, int rp, int tile_rows, float* out,
+                              int64_t out_stride, cudaStream_t st) {
+    if (tile_rows < 1 || tile_rows > 64) return cudaErrorInvalidValue;
+    const int64_t tiles = (rows + tile_rows - 1) / tile_rows;
     if (tiles <= 0) return cudaSuccess;
-    gram_tiles_kernel<<<(unsigned)tiles, 256, 0, st>>>(F, rows, r, rp, out, out_stride);
+    gram_tiles_kernel<<<(unsigned)tiles, 256, 0, st>>>(F, rows, r, rp, tile_rows, out, out_stride);
     return cudaGetLastError();
 }
 

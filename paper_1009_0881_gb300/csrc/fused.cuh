@@ -14,13 +14,13 @@ struct HalfSweepParams {
     int Na;            // rows of the factor F (= columns a of the product)
     int64_t K;         // product length
     int kchunk;        // K rows per cluster rank (multiple of the stage height)
-    int cs;            // cluster size (CTAs per 64-row tile)
+    int cs;            // cluster size (CTAs per tile of F)
     int r, rp;         // rank and padded leading dimension of F
     float* F;          // Na x rp factor, updated in place (HALS / MU)
     const float* Gin;  // gin_count Gram partial slabs (r x rp each, stride gin_stride)
     int gin_count;
     int64_t gin_stride;
-    float* Gout;       // one Gram slab per 64-row tile of F (HALS / MU)
+    float* Gout;       // one Gram slab per tile of F (HALS / MU)
     int64_t gout_stride;
     float* Pout;       // STORE mode: reduced product rows, Na x rp
     int* err_flag;     // set to 1 if a bounded wait gave up
@@ -28,10 +28,11 @@ struct HalfSweepParams {
 };
 
 struct HalfSweepLaunch {
-    CUtensorMap tmX;  // X: K rows x (>= Na) columns, box 64 x 32
+    CUtensorMap tmX;  // X: K rows x (>= Na) columns, box ba x 32
     CUtensorMap tmY;  // Y: K rows x rp columns, box br x 32
     HalfSweepParams p;
     int br;
+    int ba;  // rows of F per tile: 16, 32 or 64
     int mode;
     int tiles;
 };
@@ -45,12 +46,12 @@ cudaError_t make_tmap_f32(CUtensorMap* map, const float* base, uint64_t width, u
                           uint32_t box_w, uint32_t box_h);
 cudaError_t half_sweep_init();
 // Number of clusters of `cs` CTAs the device can hold at once (0: not schedulable).
-int half_sweep_active_clusters(int br, int r, int cs);
+int half_sweep_active_clusters(int br, int ba, int r, int cs);
 int half_sweep_stage_rows();
-size_t half_sweep_smem_bytes(int br, int r, int cs);
+size_t half_sweep_smem_bytes(int br, int ba, int r, int cs);
 cudaError_t half_sweep_launch(const HalfSweepLaunch& hl, cudaStream_t st);
-// Gram partial slabs of a tall factor, one per 64-row tile.
-cudaError_t gram_tiles_launch(const float* F, int64_t rows, int r, int rp, float* out, int64_t out_stride,
-                              cudaStream_t st);
+// Gram partial slabs of a tall factor, one per tile of `tile_rows` (<= 64) rows.
+cudaError_t gram_tiles_launch(const float* F, int64_t rows, int r, int rp, int tile_rows, float* out,
+                              int64_t out_stride, cudaStream_t st);
 
 }  // namespace nmfk

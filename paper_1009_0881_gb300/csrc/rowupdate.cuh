@@ -47,6 +47,94 @@ __device__ __forceinline__ void cluster_sum_f4(int n4, int cs, Src src, Dst dst,
     }
 }
 
+// Dn = Fn G for R rows (Fn, Dn: rows of kMaxRank floats; G: r x rp, row-major),
+// each output the sum over l = 0 .. r-1 in increasing order.  Thread (ty, tx) of
+// a 16 x 16 arrangement computes columns 4tx .. 4tx+3 of rows ty, ty+16, ...;
+// columns past rp are written as zero.
+template <int RPT>
+__device__ __forceinline__ void rows_times_gram(int R, int r, int rp, const float* Fn, const float* Gs, float* Dn) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int c0 = 4 * tx;
+    for (int rb = 0; rb < R; rb += 16 * RPT) {
+        float acc[RPT][4];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        if (c0 < rp) {
+#pragma unroll 4
+            for (int l = 0; l < r; ++l) {
+                const float4 gv = *reinterpret_cast<const float4*>(Gs + l * rp + c0);
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) {
+                    const int rr = rb + ty + 16 * i;
+                    const float fv = rr < R ? Fn[rr * kMaxRank + l] : 0.f;
+                    acc[i][0] = fmaf(fv, gv.x, acc[i][0]);
+                    acc[i][1] = fmaf(fv, gv.y, acc[i][1]);
+                    acc[i][2] = fmaf(fv, gv.z, acc[i][2]);
+                    acc[i][3] = fmaf(fv, gv.w, acc[i][3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int rr = rb + ty + 16 * i;
+            if (rr < R)
+                *reinterpret_cast<float4*>(Dn + rr * kMaxRank + c0) =
+                    make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
+    }
+}
+
+// The same product for few rows: S consecutive lanes share one group of four
+// outputs, lane s summing l = s, s + S, ..., and the S partial sums are combined
+// by butterfly shuffles.  Requires R * (rp/4) * S <= NT.
+template <int S>
+__device__ __forceinline__ void rows_times_gram_split(int R, int r, int rp, const float* Fn, const float* Gs, float* Dn) {
+    const int nq = rp / 4;
+    const int t = threadIdx.x;
+    const int o = t / S, s = t % S;
+    const bool act = o < R * nq;  // uniform over each group of S lanes
+    const int rr = act ? o / nq : 0, q = act ? o % nq : 0;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (act) {
+#pragma unroll 4
+        for (int l = s; l < r; l += S) {
+            const float4 gv = *reinterpret_cast<const float4*>(Gs + l * rp + 4 * q);
+            const float fv = Fn[rr * kMaxRank + l];
+            a0 = fmaf(fv, gv.x, a0);
+            a1 = fmaf(fv, gv.y, a1);
+            a2 = fmaf(fv, gv.z, a2);
+            a3 = fmaf(fv, gv.w, a3);
+        }
+    }
+#pragma unroll
+    for (int off = S / 2; off > 0; off >>= 1) {
+        a0 += __shfl_xor_sync(kFull, a0, off);
+        a1 += __shfl_xor_sync(kFull, a1, off);
+        a2 += __shfl_xor_sync(kFull, a2, off);
+        a3 += __shfl_xor_sync(kFull, a3, off);
+    }
+    if (act && s == 0) *reinterpret_cast<float4*>(Dn + rr * kMaxRank + 4 * q) = make_float4(a0, a1, a2, a3);
+}
+
+// Dn = Fn G for R rows, choosing the split for the number of output groups.
+__device__ __forceinline__ void rows_times_gram_any(int R, int r, int rp, const float* Fn, const float* Gs, float* Dn) {
+    const int groups = R * (rp / 4);
+    if (groups * 8 <= NT)
+        rows_times_gram_split<8>(R, r, rp, Fn, Gs, Dn);
+    else if (groups * 4 <= NT)
+        rows_times_gram_split<4>(R, r, rp, Fn, Gs, Dn);
+    else if (groups * 2 <= NT)
+        rows_times_gram_split<2>(R, r, rp, Fn, Gs, Dn);
+    else if (R <= 16)
+        rows_times_gram<1>(R, r, rp, Fn, Gs, Dn);
+    else if (R <= 32)
+        rows_times_gram<2>(R, r, rp, Fn, Gs, Dn);
+    else
+        rows_times_gram<4>(R, r, rp, Fn, Gs, Dn);
+}
+
 // Update of R rows of F (HALS or MU), RPW rows interleaved per warp.
 // Lane t owns the four consecutive entries k = 4t .. 4t+3 of each of its rows
 // (lanes 16..31 own nothing for r <= 64).  Inputs in shared memory (rows of
@@ -147,6 +235,21 @@ __device__ __forceinline__ void update_rows(float* __restrict__ F, int Na, int r
     }
 }
 
+
+// Dispatch of update_rows on the number of rows per warp: rows are interleaved
+// so that the eight warps of the CTA share the R rows.
+template <int MODE>
+__device__ __forceinline__ void update_rows_any(float* __restrict__ F, int Na, int r, int rp, int R, int64_t rowbase,
+                                                float* Fn, const float* Ared, const float* Dn, const float* Gs,
+                                                const float* Ginv) {
+    const int rpw = R <= 8 ? 1 : (R <= 16 ? 2 : (R <= 32 ? 4 : 8));
+    switch (rpw) {
+        case 1: update_rows<1, MODE>(F, Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
+        case 2: update_rows<2, MODE>(F, Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
+        case 4: update_rows<4, MODE>(F, Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
+        default: update_rows<8, MODE>(F, Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
+    }
+}
 
 }  // namespace rowupd
 }  // namespace nmfk

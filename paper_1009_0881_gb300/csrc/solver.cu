@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -116,7 +117,8 @@ struct Level {
     float* V = nullptr;  // m x rp
     GemmTask tA{}, tB{}, tC{}, tD{};  // split-K products (nmf_products)
     HalfSweepLaunch hsV{}, hsW{};     // fused half-sweeps of the solve
-    int gd_count = 0;                 // D partial slabs written by the V-step (64-row tiles of V)
+    int gd_count = 0;                 // D partial slabs written by the V-step (one per tile of V)
+    int vtile = 64;                   // rows of V per V-step tile
     // BF16 precision form: operand copies, descriptors and tcgen05 products
     __nv_bfloat16* Mb = nullptr;   // m x ldmb
     __nv_bfloat16* Mtb = nullptr;  // n x ldmtb
@@ -136,11 +138,12 @@ struct Plan {
     float* P2 = nullptr;  // C^T partials
     float* PG2 = nullptr; // D partials
     float* tmp = nullptr; // r x n staging for W
-    float* GB = nullptr;  // B = W W^T partial slabs, one per 64-row tile of Wt
+    float* GB = nullptr;  // B = W W^T partial slabs, one per tile (wtile rows) of Wt
     float* GD = nullptr;  // D = V^T V partial slabs, one per 64-row tile of V
     float* PA = nullptr;  // reduced A = M W^T rows (ANLS)
     float* PC = nullptr;  // reduced C^T = M^T V rows (ANLS)
     int gb_count = 0;
+    int wtile = 64;       // rows of Wt per W-step tile (the same on every level: the slabs are shared)
     int64_t slab = 0;     // floats per Gram slab (r x rp)
     int* err_flag = nullptr;
     double* err_part = nullptr;
@@ -191,6 +194,7 @@ struct nmf_ctx {
     std::map<std::string, GraphEntry> graphs;
     std::vector<cudaStream_t> branch_streams;  // capture branches of batched solves
     std::vector<cudaEvent_t> branch_events;
+    std::map<int, std::vector<int>> active;    // co-resident clusters of size 1..16, per kernel shape
 };
 
 namespace {
@@ -296,10 +300,10 @@ void layout(Plan& p, Bump& b, int num_sms) {
     p.PG2 = b.take<float>((size_t)max_pg2);
     p.tmp = b.take<float>((size_t)std::max<int64_t>(std::max<int64_t>(p.r * n, n * rp), p.lv[0].m * rp));
     p.slab = (int64_t)p.r * rp;
-    p.gb_count = (int)ceil_div(n, 64);
+    p.gb_count = (int)ceil_div(n, p.wtile);
     int max_gd = 1;
     for (int l = 0; l < p.L; ++l) {
-        p.lv[l].gd_count = (int)ceil_div(p.lv[l].m, 64);
+        p.lv[l].gd_count = (int)ceil_div(p.lv[l].m, p.lv[l].vtile);
         max_gd = std::max(max_gd, p.lv[l].gd_count);
     }
     p.GB = b.take<float>((size_t)(p.gb_count * p.slab));
@@ -393,20 +397,59 @@ int ensure_workspace(nmf_ctx* h, size_t bytes) {
 // the largest power of two (<= 16) whose clusters all fit on the device at once
 // (one wave; `active[i]` = co-resident clusters of size 2^i) with at least one
 // pipeline stage of K rows per rank.
-int choose_cluster(int tiles, int64_t K, const int* active) {
-    const int ks = half_sweep_stage_rows();
+// Co-resident clusters of 1, 2, 4, 8, 16 CTAs of the half-sweep kernel (cached per shape).
+const int* active_clusters(nmf_ctx* h, int br, int ba, int r) {
+    const int key = br | (ba << 8) | (r << 16);
+    auto it = h->active.find(key);
+    if (it == h->active.end()) {
+        std::vector<int> a(5);
+        for (int i = 0; i <= 4; ++i) a[i] = half_sweep_active_clusters(br, ba, r, 1 << i);
+        it = h->active.emplace(key, a).first;
+    }
+    return it->second.data();
+}
+
+// Cluster size for a half-sweep over `tiles` tiles of `ba` rows: the largest power
+// of two (<= 16, <= ba) whose clusters all fit on the device at once (one wave;
+// `active[i]` = co-resident clusters of size 2^i).  Ranks past the end of K get
+// no product work but still share the row update.
+int choose_cluster(int tiles, int ba, const int* active, int max_ctas) {
     int cs = 1;
     for (int i = 1; i <= 4; ++i) {
         const int c = 1 << i;
-        if (tiles > active[i] || ceil_div(K, c) < ks) break;
+        if (tiles > active[i] || c > ba || (int64_t)tiles * c > max_ctas) break;
         cs = c;
     }
     return cs;
 }
 
+// Tile height for a half-sweep over Na rows: the one that puts the most CTAs to
+// work (tiles x cluster size, at most one per SM); a smaller tile must bring at
+// least 1.25x as many CTAs to win, since its product loop does fewer FMAs per
+// shared-memory load and it writes more Gram slabs.  Returns the height;
+// *cs_out the cluster size.
+int choose_tile(nmf_ctx* h, int br, int r, int64_t Na, int* cs_out) {
+    int best = 64, best_cs = 1;
+    int64_t best_score = -1;
+    for (int ba : {64, 32, 16}) {
+        const int* act = active_clusters(h, br, ba, r);
+        const int64_t tiles = ceil_div(Na, ba);
+        if (tiles > act[0]) continue;
+        const int cs = choose_cluster((int)tiles, ba, act, h->num_sms);
+        const int64_t score = std::min<int64_t>(tiles * cs, h->num_sms);
+        if (best_score < 0 || 4 * score >= 5 * best_score) {
+            if (best_score >= 0 && score == best_score) continue;
+            best = ba;
+            best_cs = cs;
+            best_score = score;
+        }
+    }
+    if (cs_out) *cs_out = best_cs;
+    return best;
+}
+
 int plan_half_sweeps(nmf_ctx* h, Plan& p) {
-    int active[5];
-    for (int i = 0; i <= 4; ++i) active[i] = half_sweep_active_clusters(p.br, p.r, 1 << i);
+    const int* active_w = active_clusters(h, p.br, p.wtile, p.r);
     const int ks = half_sweep_stage_rows();
     for (int l = 0; l < p.L; ++l) {
         Level& v = p.lv[l];
@@ -414,10 +457,11 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
         HalfSweepLaunch& a = v.hsV;
         a = HalfSweepLaunch{};
         a.br = p.br;
-        a.tiles = (int)ceil_div(v.m, 64);
+        a.ba = v.vtile;
+        a.tiles = v.gd_count;
         a.p.Na = (int)v.m;
         a.p.K = p.n;
-        a.p.cs = choose_cluster(a.tiles, p.n, active);
+        a.p.cs = choose_cluster(a.tiles, a.ba, active_clusters(h, p.br, a.ba, p.r), h->num_sms);
         a.p.kchunk = (int)round_up(ceil_div(p.n, a.p.cs), ks);
         a.p.r = p.r;
         a.p.rp = p.rp;
@@ -429,17 +473,18 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
         a.p.gout_stride = p.slab;
         a.p.Pout = p.PA;
         a.p.err_flag = p.err_flag;
-        cudaError_t e = make_tmap_f32(&a.tmX, v.Mt, v.m, p.n, v.ldmt, 64, ks);
+        cudaError_t e = make_tmap_f32(&a.tmX, v.Mt, v.m, p.n, v.ldmt, v.vtile, ks);
         if (e == cudaSuccess) e = make_tmap_f32(&a.tmY, p.Wt, p.rp, p.n, p.rp, p.br, ks);
         if (e != cudaSuccess) return fail(h, NMF_ECUDA, "TMA descriptor (V-step) failed: %s", cudaGetErrorString(e));
         // W-step: X = M (m_l x n), Y = V (m_l x rp); rows of Wt
         HalfSweepLaunch& b = v.hsW;
         b = HalfSweepLaunch{};
         b.br = p.br;
+        b.ba = p.wtile;
         b.tiles = p.gb_count;
         b.p.Na = (int)p.n;
         b.p.K = v.m;
-        b.p.cs = choose_cluster(b.tiles, v.m, active);
+        b.p.cs = choose_cluster(b.tiles, b.ba, active_w, h->num_sms);
         b.p.kchunk = (int)round_up(ceil_div(v.m, b.p.cs), ks);
         b.p.r = p.r;
         b.p.rp = p.rp;
@@ -451,9 +496,13 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
         b.p.gout_stride = p.slab;
         b.p.Pout = p.PC;
         b.p.err_flag = p.err_flag;
-        e = make_tmap_f32(&b.tmX, v.M, p.n, v.m, p.ldm, 64, ks);
+        e = make_tmap_f32(&b.tmX, v.M, p.n, v.m, p.ldm, p.wtile, ks);
         if (e == cudaSuccess) e = make_tmap_f32(&b.tmY, v.V, p.rp, v.m, p.rp, p.br, ks);
         if (e != cudaSuccess) return fail(h, NMF_ECUDA, "TMA descriptor (W-step) failed: %s", cudaGetErrorString(e));
+        if (std::getenv("NMF_DEBUG_PLAN"))
+            std::fprintf(stderr, "nmf plan: level %d m=%lld n=%lld r=%d | V-step ba=%d tiles=%d cs=%d kchunk=%d | "
+                         "W-step ba=%d tiles=%d cs=%d kchunk=%d\n", l, (long long)v.m, (long long)p.n, p.r, a.ba,
+                         a.tiles, a.p.cs, a.p.kchunk, b.ba, b.tiles, b.p.cs, b.p.kchunk);
         if (p.bf16) {
             // tcgen05 operands: A tiles 128 rows x 64 K, B tiles bn rows x 64 K
             e = make_tmap_bf16_sw128(&v.tmVa, v.Mb, p.n, v.m, p.ldmb, 128);
@@ -514,6 +563,10 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
     p.rp = (int)round_up(r, 4);
     p.bf16 = h->prec == NMF_BF16;
     p.br = pick_br(p.rp);
+    // W-step tile height chosen on the finest level (the W-step tiles and their Gram
+    // slabs are shared by all levels); V-step tiles per level.  The BF16 form's row
+    // update works on 64-row tiles.
+    p.wtile = p.bf16 ? 64 : choose_tile(h, p.br, r, n, nullptr);
     p.L = L;
     p.ldm = round_up(n, 4);
     p.trace_cap = trace_cap;
@@ -526,6 +579,8 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
         hh = (hh + 1) / 2;
         ww = (ww + 1) / 2;
     }
+    for (int l = 0; l < L; ++l)
+        p.lv[l].vtile = p.bf16 ? 64 : choose_tile(h, p.br, r, p.lv[l].m, nullptr);
 }
 
 // One sweep of the inner algorithm at level l: the V-step (products M W^T and
@@ -558,7 +613,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.rows = v.m;
         u.r = p.r;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
-        if (e == cudaSuccess) e = gram_tiles_launch(v.V, v.m, p.r, p.rp, p.GD, p.slab, h->stream);
+        if (e == cudaSuccess) e = gram_tiles_launch(v.V, v.m, p.r, p.rp, v.vtile, p.GD, p.slab, h->stream);
         if (e != cudaSuccess) return e;
         *launches += 2;
     }
@@ -583,7 +638,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.rows = p.n;
         u.r = p.r;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
-        if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.GB, p.slab, h->stream);
+        if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream);
         if (e != cudaSuccess) return e;
         *launches += 2;
     }
@@ -699,7 +754,7 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
         if (ops[i].kind == OP_SWEEPS && ops[i].level == 0) last_fine = i;
     const bool stop_rule = rel_tol > 0.0 && algo != NMF_ANLS && last_fine >= 0;
     // B = W W^T slabs of the initial W, consumed by the first V-step
-    cudaError_t e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.GB, p.slab, h->stream);
+    cudaError_t e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream);
     if (e != cudaSuccess) return e;
     for (int oi = 0; oi < (int)ops.size(); ++oi) {
         const Op& op = ops[oi];
@@ -1307,7 +1362,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
-    KL(1, gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.GB, p.slab, h->stream));
+    KL(1, gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream));
     const Level& v = p.lv[0];
     const int mode = algo == NMF_HALS ? kModeHals : (algo == NMF_MU ? kModeMu : kModeStore);
     if (p.bf16) {
@@ -1375,7 +1430,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                     u.r = p.r;
                     e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
                     if (e == cudaSuccess)
-                        e = gram_tiles_launch(u.F, u.rows, p.r, p.rp, vstep ? p.GD : p.GB, p.slab, h->stream);
+                        e = gram_tiles_launch(u.F, u.rows, p.r, p.rp, vstep ? v.vtile : p.wtile, vstep ? p.GD : p.GB, p.slab, h->stream);
                     nl = 2;
                 }
             } else {
