@@ -556,6 +556,8 @@ def precision_form(args, reps=3):
 BATCH_COUNT = 64
 BATCH_LEVELS = 3
 BATCH_ITERS = {"hals": 200, "mu": 200, "anls": 20}
+# serving: per-request sweep budgets (ANLS sweeps are exact block minimisations, far costlier)
+SERVE_ITERS = {"hals": 100, "mu": 100, "anls": 8}
 BATCH_TOL = 1e-3
 
 
@@ -574,10 +576,10 @@ def batched_problems(count):
         return [f.result() for f in futs]
 
 
-def _request(p, Md, algo, V=None, W=None):
+def _request(p, Md, algo, V=None, W=None, iters=None):
     return dict(M=Md, grid_h=p.grid_h, grid_w=p.grid_w, V=p.V.copy() if V is None else V,
-                W=p.W.copy() if W is None else W, algo=algo, levels=BATCH_LEVELS, iters=BATCH_ITERS[algo],
-                rel_tol=BATCH_TOL)
+                W=p.W.copy() if W is None else W, algo=algo, levels=BATCH_LEVELS,
+                iters=(iters or BATCH_ITERS)[algo], rel_tol=BATCH_TOL)
 
 
 def batched_form(args, pool, reps=3):
@@ -648,7 +650,7 @@ def serving_form(args, pool):
     algos = ("hals", "mu", "anls")
     budget = 40 * 10**9
     out = {"rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "slots": args.serve_slots,
-           "hbm_budget_bytes": budget, "levels": BATCH_LEVELS, "iters_cap": BATCH_ITERS, "rel_tol": BATCH_TOL,
+           "hbm_budget_bytes": budget, "levels": BATCH_LEVELS, "iters_cap": SERVE_ITERS, "rel_tol": BATCH_TOL,
            "sizes": "uniform over the 64 seeded batched-form problems"}
     n_req = int(args.serve_rate * args.serve_seconds * 1.5) + 16
     gaps = synth.exponential(7, 11, n_req) / args.serve_rate
@@ -657,7 +659,7 @@ def serving_form(args, pool):
         with native.Server(0, hbm_budget_bytes=budget, slots=args.serve_slots, precision=prec) as srv:
             # warm-up: every (problem, algorithm) once, so the slots' graphs and workspaces exist
             t0 = time.perf_counter()
-            tickets = [srv.submit(_request(p, Md, a)) for p, Md in zip(pool, Mds) for a in algos]
+            tickets = [srv.submit(_request(p, Md, a, iters=SERVE_ITERS)) for p, Md in zip(pool, Mds) for a in algos]
             warm = [srv.poll(t, -1) for t in tickets]
             warm_s = time.perf_counter() - t0
             lat, outstanding, status, by_algo, held = [], {}, [], {a: 0 for a in algos}, 0
@@ -682,7 +684,7 @@ def serving_form(args, pool):
                     k = min(int(pick[i] * 3 * len(pool)), 3 * len(pool) - 1)
                     a = algos[k % 3]
                     p, Md = pool[k // 3], Mds[k // 3]
-                    outstanding[srv.submit(_request(p, Md, a))] = a
+                    outstanding[srv.submit(_request(p, Md, a, iters=SERVE_ITERS))] = a
                     by_algo[a] += 1
                     i += 1
                     t_next += gaps[i]

@@ -149,21 +149,23 @@ int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count);
 
 /*
  * nmf_workspace_bytes - device workspace nmf_solve_batch would hold on h for
- * the single problem *q (no device work); negative nmf_status on bad input.
+ * the `count` problems probs[0..count-1] (no device work); negative nmf_status
+ * on bad input.
  */
-int64_t nmf_workspace_bytes(nmf_handle h, const nmf_problem* q);
+int64_t nmf_workspace_bytes(nmf_handle h, const nmf_problem* probs, int count);
 
 /* nmf_release_workspace - free the handle's device workspace (and its cached graphs). */
 int nmf_release_workspace(nmf_handle h);
 
 /*
  * Serving form: a request loop with continuous batching.  `slots` worker slots
- * each own a handle (stream + workspace); a submitted request waits in a FIFO
- * queue until a slot is free and its workspace fits in the HBM budget
- * (sum of the workspaces held by all slots <= hbm_budget_bytes; idle slots
- * release theirs when the queue head does not fit), then runs on that slot's
- * stream while other requests run on theirs.  Each request is solved exactly
- * as nmf_solve_batch solves a single problem.
+ * each own a handle (stream + workspace).  Submitted requests wait in a FIFO
+ * queue; a free slot takes the longest run of requests from the head (at most
+ * 16) whose combined workspace fits in the HBM budget (sum of the workspaces
+ * held by all slots <= hbm_budget_bytes; idle slots release theirs when the
+ * queue head does not fit) and solves them as one nmf_solve_batch, on its own
+ * stream while other slots run theirs.  A request's result is the one
+ * nmf_solve_batch gives it alone.
  */
 typedef struct nmf_server_s* nmf_server;
 int nmf_server_create(nmf_server* out, int device, size_t hbm_budget_bytes, int slots, nmf_precision prec);

@@ -71,6 +71,7 @@ struct UpdateArgs {
     int gsplits;
     int64_t rows;
     int r;
+    double* Gd;        // ANLS: r x r scratch receiving the FP64 sum of the Gram partials
 };
 
 cudaError_t hals_update_launch(const UpdateArgs& a, int num_sms, cudaStream_t st);

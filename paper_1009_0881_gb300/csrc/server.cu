@@ -1,12 +1,14 @@
 // Serving form: continuous batching of NMF solves on one GPU (include/nmf.h).
 //
 // Requests queue in arrival order.  `slots` worker threads each own an
-// nmf_handle (stream + workspace).  A free worker takes the queue head when the
-// workspaces held by all workers, with its own grown to the head's need, fit in
-// the HBM budget; an idle worker whose workspace blocks the head releases it.
-// Requests that arrive while others are on the GPU start as soon as a slot and
-// memory free up, and their kernels overlap with the running ones (one stream
-// per slot).  Each request is one nmf_solve_batch of a single problem.
+// nmf_handle (stream + workspace).  A free worker takes the longest run of
+// requests from the queue head (at most kMaxBatch) whose combined workspace,
+// with the workspaces the other slots hold, fits in the HBM budget, and solves
+// them as one nmf_solve_batch (one CUDA graph, a branch per request).  An idle
+// worker whose workspace keeps the head from fitting releases it.  Requests
+// that arrive while others are on the GPU start as soon as a slot and memory
+// free up; their kernels overlap with the running ones (one stream per slot,
+// concurrent branches inside a batch).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -21,11 +23,12 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kMaxBatch = 16;
 
 struct Request {
     nmf_problem* prob = nullptr;
     int64_t ticket = 0;
-    size_t bytes = 0;
+    size_t bytes = 0;  // workspace of this request alone
     int status = NMF_EBUSY;
     bool done = false;
     Clock::time_point t_submit, t_done;
@@ -38,7 +41,6 @@ struct nmf_server_s {
     size_t budget = 0;
     std::vector<nmf_handle> handles;
     std::vector<size_t> held;  // workspace bytes held by each slot
-    std::vector<bool> busy;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request*> queue;
@@ -47,7 +49,7 @@ struct nmf_server_s {
     bool stop = false;
     int64_t next_ticket = 0;
     int64_t running = 0, completed = 0;
-    nmf_handle sizer = nullptr;  // for workspace estimates
+    nmf_handle sizer = nullptr;  // workspace estimates (used under mu)
 
     size_t held_except(int i) const {
         size_t s = 0;
@@ -58,20 +60,28 @@ struct nmf_server_s {
     bool fits(int i, size_t bytes) const {
         return budget == 0 || held_except(i) + std::max(held[i], bytes) <= budget;
     }
+    // Workspace of the first `count` queued requests solved together.
+    size_t group_bytes(int count) {
+        std::vector<nmf_problem> g(count);
+        for (int k = 0; k < count; ++k) g[k] = *queue[k]->prob;
+        const int64_t b = nmf_workspace_bytes(sizer, g.data(), count);
+        return b < 0 ? SIZE_MAX : (size_t)b;
+    }
 };
 
 namespace {
 
 void worker_loop(nmf_server_s* s, int i) {
     std::unique_lock<std::mutex> lk(s->mu);
+    std::vector<Request*> batch;
+    std::vector<nmf_problem> probs;
     for (;;) {
         s->cv.wait(lk, [&] { return s->stop || !s->queue.empty(); });
         if (s->queue.empty()) {
             if (s->stop) return;
             continue;
         }
-        Request* r = s->queue.front();
-        if (!s->fits(i, r->bytes)) {
+        if (!s->fits(i, s->queue.front()->bytes)) {
             // this slot is idle: give its workspace back so the head can fit, then
             // wait for running requests to finish (and their slots to do the same)
             if (s->held[i] > 0) {
@@ -85,19 +95,37 @@ void worker_loop(nmf_server_s* s, int i) {
             s->cv.wait_for(lk, std::chrono::milliseconds(1));
             continue;
         }
-        s->queue.pop_front();
-        s->held[i] = std::max(s->held[i], r->bytes);
-        s->busy[i] = true;
-        ++s->running;
+        // the longest run from the head that fits together
+        int count = 1;
+        size_t bytes = s->queue.front()->bytes;
+        const int most = std::min<int>(kMaxBatch, (int)s->queue.size());
+        while (count < most) {
+            const size_t b = s->group_bytes(count + 1);
+            if (!s->fits(i, b)) break;
+            bytes = b;
+            ++count;
+        }
+        batch.assign(s->queue.begin(), s->queue.begin() + count);
+        s->queue.erase(s->queue.begin(), s->queue.begin() + count);
+        s->held[i] = std::max(s->held[i], bytes);
+        s->running += count;
         lk.unlock();
-        const int rc = nmf_solve_batch(s->handles[i], r->prob, 1);
+        probs.resize(count);
+        for (int k = 0; k < count; ++k) probs[k] = *batch[k]->prob;
+        const int rc = nmf_solve_batch(s->handles[i], probs.data(), count);
         lk.lock();
-        r->status = rc;
-        r->done = true;
-        r->t_done = Clock::now();
-        s->busy[i] = false;
-        --s->running;
-        ++s->completed;
+        const Clock::time_point now = Clock::now();
+        for (int k = 0; k < count; ++k) {
+            Request* r = batch[k];
+            r->prob->status = probs[k].status;
+            r->prob->sweeps_run = probs[k].sweeps_run;
+            r->prob->objective = probs[k].objective;
+            r->status = probs[k].status != NMF_OK ? probs[k].status : rc;
+            r->done = true;
+            r->t_done = now;
+        }
+        s->running -= count;
+        s->completed += count;
         s->cv.notify_all();
     }
 }
@@ -128,7 +156,6 @@ int nmf_server_create(nmf_server* out, int device, size_t hbm_budget_bytes, int 
         return NMF_ECUDA;
     }
     s->held.assign(slots, 0);
-    s->busy.assign(slots, false);
     for (int i = 0; i < slots; ++i) s->workers.emplace_back(worker_loop, s, i);
     *out = s;
     return NMF_OK;
@@ -136,14 +163,14 @@ int nmf_server_create(nmf_server* out, int device, size_t hbm_budget_bytes, int 
 
 int64_t nmf_server_submit(nmf_server s, nmf_problem* prob) {
     if (!s || !prob) return NMF_EINVAL;
-    const int64_t bytes = nmf_workspace_bytes(s->sizer, prob);
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int64_t bytes = nmf_workspace_bytes(s->sizer, prob, 1);
     if (bytes < 0) return bytes;
     if (s->budget && (size_t)bytes > s->budget) return NMF_ENOMEM;
     Request* r = new Request;
     r->prob = prob;
     r->bytes = (size_t)bytes;
     r->t_submit = Clock::now();
-    std::lock_guard<std::mutex> lk(s->mu);
     r->ticket = s->next_ticket++;
     s->all[r->ticket] = r;
     s->queue.push_back(r);
@@ -168,7 +195,7 @@ int nmf_server_poll(nmf_server s, int64_t ticket, int wait_ms, double* latency_m
     const int st = r->status;
     s->all.erase(it);
     delete r;
-    return st == NMF_OK ? NMF_OK : st;
+    return st;
 }
 
 int nmf_server_stats(nmf_server s, int64_t* queued, int64_t* running, int64_t* completed, int64_t* bytes_held) {

@@ -147,6 +147,7 @@ struct Plan {
     int64_t slab = 0;     // floats per Gram slab (r x rp)
     int* err_flag = nullptr;
     double* err_part = nullptr;
+    double* Gd = nullptr;  // ANLS: FP64 Gram matrix (r x r)
     double* err_out = nullptr;
     double* d_trace = nullptr;
     int* d_status = nullptr;
@@ -312,6 +313,7 @@ void layout(Plan& p, Bump& b, int num_sms) {
     p.PC = b.take<float>((size_t)(n * rp));
     p.err_flag = b.take<int>(1);
     p.err_part = b.take<double>((size_t)error_partials_needed(p.lv[0].m, n));
+    p.Gd = b.take<double>((size_t)p.r * p.r);
     p.err_out = b.take<double>(1);
     p.d_trace = b.take<double>((size_t)(p.trace_cap > 0 ? p.trace_cap : 1));
     p.d_status = b.take<int>(1);
@@ -371,6 +373,15 @@ void layout(Plan& p, Bump& b, int num_sms) {
         v.tD.out = p.PG2;
     }
     p.bytes = b.off;
+}
+
+// Cached graphs per handle; a long-running server sees endless new batch shapes.
+constexpr size_t kMaxCachedGraphs = 256;
+
+void drop_graphs(nmf_ctx* h) {
+    cudaStreamSynchronize(h->stream);
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
 }
 
 int ensure_workspace(nmf_ctx* h, size_t bytes) {
@@ -612,10 +623,11 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.gsplits = p.gb_count;
         u.rows = v.m;
         u.r = p.r;
+        u.Gd = p.Gd;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e == cudaSuccess) e = gram_tiles_launch(v.V, v.m, p.r, p.rp, v.vtile, p.GD, p.slab, h->stream);
         if (e != cudaSuccess) return e;
-        *launches += 2;
+        *launches += 3;
     }
     HalfSweepLaunch b = v.hsW;
     b.mode = mode;
@@ -637,10 +649,11 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.gsplits = v.gd_count;
         u.rows = p.n;
         u.r = p.r;
+        u.Gd = p.Gd;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream);
         if (e != cudaSuccess) return e;
-        *launches += 2;
+        *launches += 3;
     }
     return cudaSuccess;
 }
@@ -710,6 +723,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
         u.gsplits = p.gb_count;
         u.rows = v.m;
         u.r = p.r;
+        u.Gd = p.Gd;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e != cudaSuccess) return e;
     }
@@ -739,6 +753,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
         u.gsplits = v.gd_count;
         u.rows = p.n;
         u.r = p.r;
+        u.Gd = p.Gd;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e != cudaSuccess) return e;
     }
@@ -916,6 +931,7 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
         if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return fail(h, NMF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        if (h->graphs.size() >= kMaxCachedGraphs) drop_graphs(h);
         it = h->graphs.emplace(key, ge).first;
     }
     const GraphEntry& ge = it->second;
@@ -1054,6 +1070,7 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
         if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return fail(h, NMF_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+        if (h->graphs.size() >= kMaxCachedGraphs) drop_graphs(h);
         it = h->graphs.emplace(key, ge).first;
     }
     h->launches += it->second.kernels;
@@ -1190,14 +1207,18 @@ int nmf_solve_ex(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h,
 
 int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count) { return batch_impl(h, probs, count); }
 
-int64_t nmf_workspace_bytes(nmf_handle h, const nmf_problem* q) {
-    if (!h || !q) return NMF_EINVAL;
-    int rc = check_dims(h, q->m, q->n, q->r);
-    if (rc) return rc;
-    if (q->grid_h < 1 || q->grid_w < 1 || (int64_t)q->grid_h * q->grid_w != q->m || q->levels < 1 || q->levels > 16)
-        return fail(h, NMF_EINVAL, "bad problem geometry");
-    std::vector<Plan> plans(1);
-    plan_dims(h, plans[0], q->m, q->n, q->grid_h, q->grid_w, q->r, q->levels, 0);
+int64_t nmf_workspace_bytes(nmf_handle h, const nmf_problem* probs, int count) {
+    if (!h || !probs || count < 1) return NMF_EINVAL;
+    std::vector<Plan> plans(count);
+    for (int i = 0; i < count; ++i) {
+        const nmf_problem* q = probs + i;
+        int rc = check_dims(h, q->m, q->n, q->r);
+        if (rc) return rc;
+        if (q->grid_h < 1 || q->grid_w < 1 || (int64_t)q->grid_h * q->grid_w != q->m || q->levels < 1 ||
+            q->levels > 16)
+            return fail(h, NMF_EINVAL, "problem %d: bad geometry", i);
+        plan_dims(h, plans[i], q->m, q->n, q->grid_h, q->grid_w, q->r, q->levels, 0);
+    }
     return (int64_t)plans_bytes(h, plans);
 }
 
@@ -1428,10 +1449,12 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                     u.gsplits = vstep ? p.gb_count : v.gd_count;
                     u.rows = vstep ? v.m : p.n;
                     u.r = p.r;
+                    u.Gd = p.Gd;
                     e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
                     if (e == cudaSuccess)
-                        e = gram_tiles_launch(u.F, u.rows, p.r, p.rp, vstep ? v.vtile : p.wtile, vstep ? p.GD : p.GB, p.slab, h->stream);
-                    nl = 2;
+                        e = gram_tiles_launch(u.F, u.rows, p.r, p.rp, vstep ? v.vtile : p.wtile, vstep ? p.GD : p.GB,
+                                              p.slab, h->stream);
+                    nl = 3;
                 }
             } else {
                 e = error_launch(v.M, p.ldm, v.V, p.Wt, p.rp, m, n, r, p.err_part, p.err_out, h->stream);

@@ -175,85 +175,151 @@ __device__ __forceinline__ double warp_min(double v) {
     return v;
 }
 
-// Solve G_PP z_P = b_P for the passive set `mask` by Cholesky; z = 0 off P.
-// Returns false if a pivot falls below 1e-12 of its original diagonal (the
-// passive columns are numerically dependent).
-__device__ bool solve_passive(const double* G, int r, uint64_t mask, const double b[2], double z[2],
-                              double* L, double* y, int* pidx, int lane) {
-    const int p = __popcll(mask);
+// Cholesky factor L (row stride r) of G restricted to the passive variables
+// ord[0..p), kept in the order the variables entered; inv[k] = position of k;
+// dinv[i] = 1 / L_ii (the solves then need no division, which costs about ten
+// FP64 multiply-adds).  Full factorization of the set `mask` (variables in
+// increasing index order).  Returns false if a pivot falls below 1e-12 of its
+// original diagonal (the passive columns are numerically dependent).
+__device__ bool chol_full(const double* G, int r, uint64_t mask, double* L, double* dinv, int* ord, int* inv, int& p,
+                          int lane) {
+    p = __popcll(mask);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const int k = lane + 32 * s;
         if (k < r && ((mask >> k) & 1ull)) {
             const int pos = __popcll(mask & ((1ull << k) - 1ull));
-            pidx[pos] = k;
-            y[pos] = b[s];
+            ord[pos] = k;
+            inv[k] = pos;
         }
     }
     __syncwarp();
     for (int e = lane; e < p * p; e += 32) {
         const int i = e / p, j = e - i * p;
-        L[e] = G[pidx[i] * r + pidx[j]];
+        if (j <= i) L[i * r + j] = G[ord[i] * r + ord[j]];
     }
     __syncwarp();
-    bool ok = true;
     for (int k = 0; k < p; ++k) {
-        const double d0 = L[k * p + k];
-        const double orig = G[pidx[k] * r + pidx[k]];
-        if (!(d0 > 1e-12 * orig)) {
-            ok = false;
-            break;
+        const double d0 = L[k * r + k];
+        if (!(d0 > 1e-12 * G[ord[k] * r + ord[k]])) return false;  // uniform over the warp
+        const double d = sqrt(d0), di = 1.0 / d;
+        __syncwarp();
+        if (lane == 0) {
+            L[k * r + k] = d;
+            dinv[k] = di;
         }
-        const double d = sqrt(d0);
+        for (int i = k + 1 + lane; i < p; i += 32) L[i * r + k] *= di;
         __syncwarp();
-        if (lane == 0) L[k * p + k] = d;
-        for (int i = k + 1 + lane; i < p; i += 32) L[i * p + k] /= d;
-        __syncwarp();
-        for (int i = k + 1 + lane; i < p; i += 32) {
-            const double lik = L[i * p + k];
-            for (int j = k + 1; j <= i; ++j) L[i * p + j] -= lik * L[j * p + k];
+        // trailing update of the lower triangle, entries spread evenly over the lanes
+        const int nt = p - k - 1;
+        if (nt > 0) {
+            int i = lane / nt, j = lane - (lane / nt) * nt;
+            const int di2 = 32 / nt, dj = 32 - di2 * nt;
+            for (int e = lane; e < nt * nt; e += 32) {
+                if (j <= i) L[(k + 1 + i) * r + (k + 1 + j)] -= L[(k + 1 + i) * r + k] * L[(k + 1 + j) * r + k];
+                i += di2;
+                j += dj;
+                if (j >= nt) {
+                    j -= nt;
+                    ++i;
+                }
+            }
         }
         __syncwarp();
     }
-    if (ok) {
-        // forward substitution L y = b_P
-        for (int j = 0; j < p; ++j) {
-            const double yj = y[j] / L[j * p + j];
-            __syncwarp();
-            if (lane == 0) y[j] = yj;
-            for (int i = j + 1 + lane; i < p; i += 32) y[i] -= L[i * p + j] * yj;
-            __syncwarp();
-        }
-        // back substitution L^T z = y
-        for (int j = p - 1; j >= 0; --j) {
-            const double zj = y[j] / L[j * p + j];
-            __syncwarp();
-            if (lane == 0) y[j] = zj;
-            for (int i = lane; i < j; i += 32) y[i] -= L[j * p + i] * zj;
-            __syncwarp();
-        }
+    return true;
+}
+
+// Append variable j to the factor: solve L l = G[ord, j] by forward
+// substitution, then l_jj = sqrt(G_jj - l.l).  False (factor unchanged) if
+// column j is numerically dependent on the passive ones.
+__device__ bool chol_append(const double* G, int r, int j, double* L, double* dinv, int* ord, int* inv, int& p,
+                            double* y, int lane) {
+    for (int i = lane; i < p; i += 32) y[i] = G[ord[i] * r + j];
+    __syncwarp();
+    for (int k = 0; k < p; ++k) {
+        const double lk = y[k] * dinv[k];
+        __syncwarp();
+        if (lane == 0) y[k] = lk;
+        for (int i = k + 1 + lane; i < p; i += 32) y[i] -= L[i * r + k] * lk;
+        __syncwarp();
+    }
+    double ss = 0.0;
+    for (int i = lane; i < p; i += 32) ss += y[i] * y[i];
+    ss = warp_sum(ss);
+    const double gjj = G[j * r + j];
+    const double d0 = gjj - ss;
+    if (!(d0 > 1e-12 * gjj)) return false;
+    for (int i = lane; i < p; i += 32) L[p * r + i] = y[i];
+    if (lane == 0) {
+        const double d = sqrt(d0);
+        L[p * r + p] = d;
+        dinv[p] = 1.0 / d;
+        ord[p] = j;
+        inv[j] = p;
+    }
+    ++p;
+    __syncwarp();
+    return true;
+}
+
+// z_P = G_PP^{-1} b_P from the factor (forward and back substitution); z = 0 off P.
+__device__ void chol_solve(const double* L, const double* dinv, int r, const int* ord, const int* inv, int p,
+                           uint64_t mask, const double* bs, double z[2], double* y, int lane) {
+    for (int i = lane; i < p; i += 32) y[i] = bs[ord[i]];
+    __syncwarp();
+    for (int j = 0; j < p; ++j) {
+        const double yj = y[j] * dinv[j];
+        __syncwarp();
+        if (lane == 0) y[j] = yj;
+        for (int i = j + 1 + lane; i < p; i += 32) y[i] -= L[i * r + j] * yj;
+        __syncwarp();
+    }
+    for (int j = p - 1; j >= 0; --j) {
+        const double zj = y[j] * dinv[j];
+        __syncwarp();
+        if (lane == 0) y[j] = zj;
+        for (int i = lane; i < j; i += 32) y[i] -= L[j * r + i] * zj;
+        __syncwarp();
     }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const int k = lane + 32 * s;
-        z[s] = 0.0;
-        if (ok && k < r && ((mask >> k) & 1ull)) z[s] = y[__popcll(mask & ((1ull << k) - 1ull))];
+        z[s] = (k < r && ((mask >> k) & 1ull)) ? y[inv[k]] : 0.0;
     }
     __syncwarp();
-    return ok;
+}
+
+// Per-warp shared memory of the ANLS kernel in doubles: L (r x r), dinv, y, bs.
+__host__ __device__ inline size_t anls_warp_doubles(int r) { return (size_t)r * r + 3 * kMaxRank; }
+
+// G = sum of the Gram partial slabs in FP64 (slabs in index order), once per
+// half-sweep, for all the ANLS rows.
+__global__ void gram_reduce_f64_kernel(const UpdateArgs u) {
+    const int r = u.r;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= r * r) return;
+    const int l = idx / r, k = idx - l * r;
+    const float* p = u.PG + (int64_t)l * u.ldpg + k;
+    double s = 0;
+    for (int q = 0; q < u.gsplits; ++q) s += (double)p[(int64_t)q * u.pgs];
+    u.Gd[idx] = s;
 }
 
 __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const UpdateArgs u, int* status) {
     extern __shared__ double smem[];
     const int r = u.r;
     double* G = smem;  // r x r
-    reduce_gram<double>(u, G);
+    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) G[idx] = u.Gd[idx];
+    __syncthreads();
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    double* L = G + r * r + (size_t)warp * r * r;
-    double* y = G + r * r + (size_t)kAnlsWarps * r * r + warp * kMaxRank;
-    int* pidx = reinterpret_cast<int*>(G + r * r + (size_t)kAnlsWarps * r * r + kAnlsWarps * kMaxRank) +
-                warp * kMaxRank;
+    double* L = G + r * r + (size_t)warp * anls_warp_doubles(r);
+    double* dinv = L + (size_t)r * r;
+    double* y = dinv + kMaxRank;
+    double* bs = y + kMaxRank;
+    int* ord = reinterpret_cast<int*>(G + r * r + (size_t)kAnlsWarps * anls_warp_doubles(r)) + warp * 2 * kMaxRank;
+    int* inv = ord + kMaxRank;
     const uint64_t all = (r == 64) ? ~0ull : ((1ull << r) - 1ull);
 
     for (int64_t row = (int64_t)blockIdx.x * kAnlsWarps + warp; row < u.rows;
@@ -265,26 +331,30 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
             const int k = lane + 32 * s;
             b[s] = 0.0;
             if (k < r) {
-                const float* p = u.P + row * u.ldp + k;
+                const float* pp = u.P + row * u.ldp + k;
                 double acc = 0.0;
-                for (int q = 0; q < u.splits; ++q) acc += (double)p[(int64_t)q * u.ps];
+                for (int q = 0; q < u.splits; ++q) acc += (double)pp[(int64_t)q * u.ps];
                 b[s] = acc;
+                bs[k] = acc;
             }
             const bool pos = k < r && u.F[row * u.ldf + k] > 0.f;
             warm |= (uint64_t)__ballot_sync(kFull, pos) << (32 * s);
         }
+        __syncwarp();
         const double bmax = warp_max(fmax(fabs(b[0]), fabs(b[1])));
         const double tol = 1e-12 * fmax(1.0, bmax);
         uint64_t mask = 0, excluded = 0;
+        int p = 0;
 
         // Warm start from the support of the incoming row: drop the variables
         // whose unconstrained solution is not positive until the rest is.
         mask = warm & all;
         for (int it = 0; it <= r && mask; ++it) {
-            if (!solve_passive(G, r, mask, b, z, L, y, pidx, lane)) {
+            if (!chol_full(G, r, mask, L, dinv, ord, inv, p, lane)) {
                 mask = 0;
                 break;
             }
+            chol_solve(L, dinv, r, ord, inv, p, mask, bs, z, y, lane);
             uint64_t badm = 0;
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -299,7 +369,10 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
             }
             mask &= ~badm;
         }
-        if (!mask) x[0] = x[1] = 0.0;
+        if (!mask) {
+            x[0] = x[1] = 0.0;
+            p = 0;
+        }
 
         bool capped = false;
         for (int outer = 0;; ++outer) {
@@ -339,13 +412,14 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
                 capped = true;
                 break;
             }
+            // the factor of the passive set grows by one column
+            if (!chol_append(G, r, j, L, dinv, ord, inv, p, y, lane)) {
+                excluded |= 1ull << j;
+                continue;
+            }
             mask |= 1ull << j;
             for (int it = 0; it <= r; ++it) {
-                if (!solve_passive(G, r, mask, b, z, L, y, pidx, lane)) {
-                    mask &= ~(1ull << j);
-                    excluded |= 1ull << j;
-                    break;
-                }
+                chol_solve(L, dinv, r, ord, inv, p, mask, bs, z, y, lane);
                 uint64_t badm = 0;
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
@@ -383,6 +457,18 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
                     const int k = lane + 32 * s;
                     if (k >= r || !((mask >> k) & 1ull)) x[s] = 0.0;
                 }
+                // the passive set shrank: refactor it
+                if (!chol_full(G, r, mask, L, dinv, ord, inv, p, lane)) {
+                    mask &= ~(1ull << j);
+                    excluded |= 1ull << j;
+                    if ((j & 31) == lane) x[j >> 5] = 0.0;
+                    if (!chol_full(G, r, mask, L, dinv, ord, inv, p, lane)) {
+                        mask = 0;
+                        p = 0;
+                        x[0] = x[1] = 0.0;
+                    }
+                    break;
+                }
             }
         }
         if (capped && lane == 0) atomicOr(status, 1);
@@ -405,8 +491,8 @@ cudaError_t mu_update_launch(const UpdateArgs& a, int num_sms, cudaStream_t st) 
 }
 
 static size_t anls_smem_bytes(int r) {
-    return sizeof(double) * ((size_t)r * r * (1 + kAnlsWarps) + kAnlsWarps * kMaxRank) +
-           sizeof(int) * kAnlsWarps * kMaxRank;
+    return sizeof(double) * ((size_t)r * r + kAnlsWarps * anls_warp_doubles(r)) +
+           sizeof(int) * kAnlsWarps * 2 * kMaxRank;
 }
 
 cudaError_t init_kernel_attributes() {
@@ -417,6 +503,8 @@ cudaError_t init_kernel_attributes() {
 cudaError_t anls_update_launch(const UpdateArgs& u, int num_sms, int* d_status, cudaStream_t st) {
     if (u.rows <= 0) return cudaSuccess;
     const size_t smem = anls_smem_bytes(u.r);
+    if (!u.Gd) return cudaErrorInvalidValue;
+    gram_reduce_f64_kernel<<<(unsigned)ceil_div((int64_t)u.r * u.r, 256), 256, 0, st>>>(u);
     int64_t grid = ceil_div(u.rows, kAnlsWarps);
     const int64_t cap = 8LL * num_sms;
     if (grid > cap) grid = cap;

@@ -45,7 +45,7 @@ SIGNATURES = [
     ("nmf_profile_sweep", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
     ("nmf_error_noalloc", _I, [_P, _P, _P, _I64, _I64, _I, _P, ctypes.POINTER(ctypes.c_double)]),
     ("nmf_solve_batch", _I, [_P, _P, _I]),
-    ("nmf_workspace_bytes", _I64, [_P, _P]),
+    ("nmf_workspace_bytes", _I64, [_P, _P, _I]),
     ("nmf_release_workspace", _I, [_P]),
     ("nmf_server_create", _I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I, _I]),
     ("nmf_server_submit", _I64, [_P, _P]),
@@ -198,9 +198,13 @@ class Handle:
             self._rc(rc)
         return out
 
-    def workspace_bytes(self, d: dict) -> int:
-        """nmf_workspace_bytes: device bytes one problem dict needs (nothing is allocated)."""
-        b = int(self.lib.nmf_workspace_bytes(self.h, ctypes.byref(fill_problem(Problem(), d))))
+    def workspace_bytes(self, d) -> int:
+        """nmf_workspace_bytes: device bytes for a problem dict, or a list of them solved together."""
+        ds = d if isinstance(d, (list, tuple)) else [d]
+        arr = (Problem * len(ds))()
+        for q, x in zip(arr, ds):
+            fill_problem(q, x)
+        b = int(self.lib.nmf_workspace_bytes(self.h, ctypes.cast(arr, _P), len(ds)))
         if b < 0:
             self._rc(b)
         return b
