@@ -157,7 +157,7 @@ cudaError_t rows_update_launch(const UpdateArgs& u, int num_sms, bool hals, cuda
 // ANLS: warp-per-row Lawson-Hanson NNLS in FP64.
 // Distributed vectors: entry k lives in lane k & 31, slot k >> 5.
 // ---------------------------------------------------------------------------
-constexpr int kAnlsWarps = 4;
+constexpr int kAnlsWarps = 8;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -175,7 +175,10 @@ __device__ __forceinline__ double warp_min(double v) {
     return v;
 }
 
-// Cholesky factor L (row stride r) of G restricted to the passive variables
+// Row i of the packed lower-triangular factor starts at tri(i).
+__device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
+
+// Cholesky factor L (packed lower triangle) of G restricted to the passive variables
 // ord[0..p), kept in the order the variables entered; inv[k] = position of k;
 // dinv[i] = 1 / L_ii (the solves then need no division, which costs about ten
 // FP64 multiply-adds).  Full factorization of the set `mask` (variables in
@@ -196,19 +199,19 @@ __device__ bool chol_full(const double* G, int r, uint64_t mask, double* L, doub
     __syncwarp();
     for (int e = lane; e < p * p; e += 32) {
         const int i = e / p, j = e - i * p;
-        if (j <= i) L[i * r + j] = G[ord[i] * r + ord[j]];
+        if (j <= i) L[tri(i) + j] = G[ord[i] * r + ord[j]];
     }
     __syncwarp();
     for (int k = 0; k < p; ++k) {
-        const double d0 = L[k * r + k];
+        const double d0 = L[tri(k) + k];
         if (!(d0 > 1e-12 * G[ord[k] * r + ord[k]])) return false;  // uniform over the warp
         const double d = sqrt(d0), di = 1.0 / d;
         __syncwarp();
         if (lane == 0) {
-            L[k * r + k] = d;
+            L[tri(k) + k] = d;
             dinv[k] = di;
         }
-        for (int i = k + 1 + lane; i < p; i += 32) L[i * r + k] *= di;
+        for (int i = k + 1 + lane; i < p; i += 32) L[tri(i) + k] *= di;
         __syncwarp();
         // trailing update of the lower triangle, entries spread evenly over the lanes
         const int nt = p - k - 1;
@@ -216,7 +219,10 @@ __device__ bool chol_full(const double* G, int r, uint64_t mask, double* L, doub
             int i = lane / nt, j = lane - (lane / nt) * nt;
             const int di2 = 32 / nt, dj = 32 - di2 * nt;
             for (int e = lane; e < nt * nt; e += 32) {
-                if (j <= i) L[(k + 1 + i) * r + (k + 1 + j)] -= L[(k + 1 + i) * r + k] * L[(k + 1 + j) * r + k];
+                if (j <= i) {
+                    const int ti = tri(k + 1 + i);
+                    L[ti + (k + 1 + j)] -= L[ti + k] * L[tri(k + 1 + j) + k];
+                }
                 i += di2;
                 j += dj;
                 if (j >= nt) {
@@ -241,7 +247,7 @@ __device__ bool chol_append(const double* G, int r, int j, double* L, double* di
         const double lk = y[k] * dinv[k];
         __syncwarp();
         if (lane == 0) y[k] = lk;
-        for (int i = k + 1 + lane; i < p; i += 32) y[i] -= L[i * r + k] * lk;
+        for (int i = k + 1 + lane; i < p; i += 32) y[i] -= L[tri(i) + k] * lk;
         __syncwarp();
     }
     double ss = 0.0;
@@ -250,10 +256,10 @@ __device__ bool chol_append(const double* G, int r, int j, double* L, double* di
     const double gjj = G[j * r + j];
     const double d0 = gjj - ss;
     if (!(d0 > 1e-12 * gjj)) return false;
-    for (int i = lane; i < p; i += 32) L[p * r + i] = y[i];
+    for (int i = lane; i < p; i += 32) L[tri(p) + i] = y[i];
     if (lane == 0) {
         const double d = sqrt(d0);
-        L[p * r + p] = d;
+        L[tri(p) + p] = d;
         dinv[p] = 1.0 / d;
         ord[p] = j;
         inv[j] = p;
@@ -272,14 +278,14 @@ __device__ void chol_solve(const double* L, const double* dinv, int r, const int
         const double yj = y[j] * dinv[j];
         __syncwarp();
         if (lane == 0) y[j] = yj;
-        for (int i = j + 1 + lane; i < p; i += 32) y[i] -= L[i * r + j] * yj;
+        for (int i = j + 1 + lane; i < p; i += 32) y[i] -= L[tri(i) + j] * yj;
         __syncwarp();
     }
     for (int j = p - 1; j >= 0; --j) {
         const double zj = y[j] * dinv[j];
         __syncwarp();
         if (lane == 0) y[j] = zj;
-        for (int i = lane; i < j; i += 32) y[i] -= L[j * r + i] * zj;
+        for (int i = lane; i < j; i += 32) y[i] -= L[tri(j) + i] * zj;
         __syncwarp();
     }
 #pragma unroll
@@ -290,8 +296,8 @@ __device__ void chol_solve(const double* L, const double* dinv, int r, const int
     __syncwarp();
 }
 
-// Per-warp shared memory of the ANLS kernel in doubles: L (r x r), dinv, y, bs.
-__host__ __device__ inline size_t anls_warp_doubles(int r) { return (size_t)r * r + 3 * kMaxRank; }
+// Per-warp shared memory of the ANLS kernel in doubles: L (packed, r (r+1)/2), dinv, y, bs.
+__host__ __device__ inline size_t anls_warp_doubles(int r) { return (size_t)r * (r + 1) / 2 + 3 * kMaxRank; }
 
 // G = sum of the Gram partial slabs in FP64 (slabs in index order), once per
 // half-sweep, for all the ANLS rows.
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     double* L = G + r * r + (size_t)warp * anls_warp_doubles(r);
-    double* dinv = L + (size_t)r * r;
+    double* dinv = L + (size_t)r * (r + 1) / 2;
     double* y = dinv + kMaxRank;
     double* bs = y + kMaxRank;
     int* ord = reinterpret_cast<int*>(G + r * r + (size_t)kAnlsWarps * anls_warp_doubles(r)) + warp * 2 * kMaxRank;
