@@ -403,10 +403,10 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
 # valid while the kernel's sources hash to `src`; the captures and their commands are
 # summarised under profiles/.
 TRAFFIC = {
-    "half_sweep_kernel": {"bytes": 0.5 * (4.581888e6 + 4.233216e6), "src": "f9a05243749f2b37",
+    "half_sweep_kernel": {"bytes": 0.5 * (4.969728e6 + 4.234240e6), "src": "bce7ce732e28e11d",
                           "files": ("fused.cu", "fused.cuh", "rowupdate.cuh", "ptx.cuh", "nmf_internal.cuh"),
-                          "scope": "mean of the finest-level V-step and W-step launches, 19x19 grid n=2429 r=49"},
-    "tc_gemm_kernel": {"bytes": 262.546176e6 + 13.465856e6, "src": "48475781f0146f45",
+                          "scope": "mean of the finest-level V-step (64-row tiles) and W-step (32-row tiles) launches, 19x19 grid n=2429 r=49"},
+    "tc_gemm_kernel": {"bytes": 262.664448e6 + 13.502976e6, "src": "12584d2ec50ae58f",
                        "files": ("tc_gemm.cu", "tc_gemm.cuh", "ptx.cuh", "nmf_internal.cuh"),
                        "scope": "finest-level V-step product, 256x256 grid n=2000 r=64"},
 }
