@@ -1,3 +1,4 @@
+#include <algorithm>
 // Kernels around the tcgen05 products of the BF16 precision form: BF16 operand
 // copies, the final Gram matrix from per-tile slabs, and the row update.
 //
@@ -46,13 +47,70 @@ __global__ void to_bf16_t_kernel(const float* __restrict__ in, int64_t ldi, int6
     }
 }
 
+// G[e] = sum of the slabs, in two levels so that thousands of slabs do not
+// serialise on one thread: block (x, y) sums slab chunk y of outputs
+// 256x .. 256x+255 into part[y], and the last block of column x to finish
+// (ticket in cnt[x], reset afterwards) adds the chunk sums in chunk order.
 __global__ void gram_final_kernel(const float* __restrict__ slabs, int count, int64_t stride, int n,
-                                  float* __restrict__ G, const int* skip) {
+                                  float* __restrict__ G, float* __restrict__ part, int* cnt, const int* skip) {
+    if (skip && *(volatile const int*)skip) return;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n || (skip && *(volatile const int*)skip)) return;
-    float s = 0.f;
-    for (int q = 0; q < count; ++q) s += slabs[(int64_t)q * stride + e];
-    G[e] = s;
+    const int S = gridDim.y, y = blockIdx.y;
+    const int per = (count + S - 1) / S;
+    const int q0 = y * per, q1 = min(count, q0 + per);
+    if (e < n) {
+        float s = 0.f;
+        for (int q = q0; q < q1; ++q) s += slabs[(int64_t)q * stride + e];
+        part[(int64_t)y * n + e] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int last;
+    if (threadIdx.x == 0) last = atomicAdd(&cnt[blockIdx.x], 1) == S - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (e < n) {
+        float s = 0.f;
+        for (int k = 0; k < S; ++k) s += *(volatile const float*)&part[(int64_t)k * n + e];
+        G[e] = s;
+    }
+    if (threadIdx.x == 0) cnt[blockIdx.x] = 0;
+}
+
+constexpr int TLD = BA + 1;  // row stride of the transposed tiles (odd: conflict-free columns)
+
+// HALS update (Algorithm HALS) of the BA rows of a tile, one thread per row:
+// the thread keeps g = P_i - F_i G of its row in registers and walks the
+// columns k = 0 .. r-1 in order, F_ik <- max(0, F_ik + g_k / G_kk), then
+// g_j -= delta G_kj for the later columns j.  The register array is shifted
+// by one column per step (g[0] is always the current g_k), so the loop over k
+// stays rolled (compact code) while every register index is static; Gsk holds
+// row k of G shifted the same way, Gsk[k][j] = G[k][k+1+j] (zero past r).
+// FT / GT hold F and g transposed (column k of the tile at FT + k * TLD).
+template <int RB>
+__device__ __forceinline__ void hals_rows_lane(int r, float* FT, const float* GT, const float* Gsk, const float* Ginv) {
+    const int rr = threadIdx.x;
+    if (rr >= BA) return;
+    float g[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) g[k] = GT[k * TLD + rr];
+#pragma unroll 1
+    for (int k = 0; k < r; ++k) {
+        const float fk = FT[k * TLD + rr];
+        const float nv = fmaxf(0.f, fmaf(g[0], Ginv[k], fk));
+        const float d = nv - fk;
+        FT[k * TLD + rr] = nv;
+        const float4* gk = reinterpret_cast<const float4*>(Gsk + k * kMaxRank);
+#pragma unroll
+        for (int q = 0; q < RB / 4; ++q) {
+            const float4 gv = gk[q];
+            g[4 * q + 0] = fmaf(-d, gv.x, g[4 * q + 1]);
+            g[4 * q + 1] = fmaf(-d, gv.y, g[4 * q + 2]);
+            g[4 * q + 2] = fmaf(-d, gv.z, g[4 * q + 3]);
+            g[4 * q + 3] = 4 * q + 4 < RB ? fmaf(-d, gv.w, g[(4 * q + 4) % RB]) : 0.f;
+        }
+    }
 }
 
 template <int MODE>
@@ -66,6 +124,9 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
     float* Ared = Fn + BA * kMaxRank;     // BA x kMaxRank
     float* Dn = Ared + BA * kMaxRank;     // BA x kMaxRank
     float* Fg = Dn + BA * kMaxRank;       // r x rp
+    float* FT = Fg + r * rp;              // kMaxRank x TLD (HALS: F transposed)
+    float* GT = FT + kMaxRank * TLD;      // kMaxRank x TLD (HALS: g transposed)
+    float* G64 = GT + kMaxRank * TLD;     // kMaxRank x kMaxRank (HALS: shifted rows of G, see hals_rows_lane)
     const int tid = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * BA;
     const int R = BA;
@@ -105,7 +166,43 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
         for (int k = tid; k < kMaxRank; k += NT) Ginv[k] = (k < r && Gs[k * rp + k] > 0.f) ? 1.f / Gs[k * rp + k] : 0.f;
         rowupd::rows_times_gram<4>(R, r, rp, Fn, Gs, Dn);
         __syncthreads();
-        rowupd::update_rows_any<MODE>(q.F, (int)q.rows, r, rp, R, row0, Fn, Ared, Dn, Gs, Ginv);
+        if (MODE == rowupd::kModeHals) {
+            // transposed F and g = P - F G (zero past rp), zero-padded G
+            for (int e = tid; e < BA * kMaxRank; e += NT) {
+                const int rr = e / kMaxRank, k = e - rr * kMaxRank;
+                FT[k * TLD + rr] = Fn[e];
+                GT[k * TLD + rr] = k < rp ? Ared[e] - Dn[e] : 0.f;
+            }
+            for (int e = tid; e < kMaxRank * kMaxRank; e += NT) {
+                const int k = e / kMaxRank, j = k + 1 + (e - k * kMaxRank);
+                G64[e] = (k < r && j < r) ? Gs[k * rp + j] : 0.f;
+            }
+            __syncthreads();
+            if (r <= 16)
+                hals_rows_lane<16>(r, FT, GT, G64, Ginv);
+            else if (r <= 32)
+                hals_rows_lane<32>(r, FT, GT, G64, Ginv);
+            else if (r <= 48)
+                hals_rows_lane<48>(r, FT, GT, G64, Ginv);
+            else
+                hals_rows_lane<64>(r, FT, GT, G64, Ginv);
+            __syncthreads();
+            // new rows back to row-major, and to the factor in global memory
+            for (int e = tid; e < BA * kMaxRank; e += NT) {
+                const int rr = e / kMaxRank, k = e - rr * kMaxRank;
+                Fn[e] = FT[k * TLD + rr];
+            }
+            __syncthreads();
+            for (int e = tid; e < BA * Q4; e += NT) {
+                const int rr = e / Q4, k4 = e - rr * Q4;
+                const int64_t row = row0 + rr;
+                if (row < q.rows)
+                    *reinterpret_cast<float4*>(q.F + row * rp + 4 * k4) =
+                        *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + 4 * k4);
+            }
+        } else {
+            rowupd::update_rows_any<MODE>(q.F, (int)q.rows, r, rp, R, row0, Fn, Ared, Dn, Gs, Ginv);
+        }
         __syncthreads();
     } else {
         // rows past the end read as zero already; nothing to update
@@ -117,7 +214,8 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
         for (int e = tid; e < r * BA; e += NT) {
             const int k = e / BA, rr = e - k * BA;
             const int64_t row = row0 + rr;
-            if (row < q.rows) q.Fb[(int64_t)k * q.ldb + row] = __float2bfloat16_rn(Fn[rr * kMaxRank + k]);
+            const float v = MODE == rowupd::kModeHals ? FT[k * TLD + rr] : Fn[rr * kMaxRank + k];
+            if (row < q.rows) q.Fb[(int64_t)k * q.ldb + row] = __float2bfloat16_rn(v);
         }
     }
     // Gram slab of the tile, 4 x 4 outputs per thread
@@ -149,7 +247,8 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
 }
 
 size_t rows_smem_bytes(int r, int rp) {
-    return sizeof(float) * ((size_t)2 * r * rp + kMaxRank + 3 * BA * kMaxRank);
+    return sizeof(float) * ((size_t)2 * r * rp + kMaxRank + 3 * BA * kMaxRank + 2 * kMaxRank * TLD +
+                            kMaxRank * kMaxRank);
 }
 
 }  // namespace
@@ -174,10 +273,12 @@ cudaError_t to_bf16_launch(const float* in, int64_t ldi, int64_t rows, int64_t c
     return cudaGetLastError();
 }
 
-cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int r, int rp, float* G, cudaStream_t st,
-                              const int* skip) {
+cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int r, int rp, float* G, float* part,
+                              int* cnt, cudaStream_t st, const int* skip) {
     const int n = r * rp;
-    gram_final_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(slabs, count, stride, n, G, skip);
+    const int S = (int)std::min<int64_t>(kGramChunks, std::max<int64_t>(1, ceil_div(count, 16)));
+    gram_final_kernel<<<dim3((unsigned)ceil_div(n, 256), (unsigned)S), 256, 0, st>>>(slabs, count, stride, n, G, part,
+                                                                                     cnt, skip);
     return cudaGetLastError();
 }
 

@@ -162,6 +162,8 @@ struct Plan {
     float* P1b = nullptr;             // split partials of A = M W^T
     float* P2b = nullptr;             // split partials of C^T = M^T V
     float* Gfin = nullptr;            // reduced Gram matrix, r x rp
+    float* Gpart = nullptr;           // chunk sums of the Gram slabs (kGramChunks x r x rp)
+    int* gcnt = nullptr;              // tickets of the two-level slab sum (zero between launches)
     // stopping rule of the batched form
     double* conv_state = nullptr;     // [0] previous objective, [1] current, [2] final
     int* conv_flag = nullptr;
@@ -326,6 +328,8 @@ void layout(Plan& p, Bump& b, int num_sms) {
         p.ldmb = round_up(n, 8);
         p.Wb = b.take<__nv_bfloat16>((size_t)(p.r * p.ldmb));
         p.Gfin = b.take<float>((size_t)p.slab);
+        p.Gpart = b.take<float>((size_t)kGramChunks * p.slab);
+        p.gcnt = b.take<int>((size_t)ceil_div(p.slab, 256));
         int64_t max_p1b = 0, max_p2b = 0;
         for (int l = 0; l < p.L; ++l) {
             Level& v = p.lv[l];
@@ -693,7 +697,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
     gV.skip = skip;
     gW.skip = skip;
     cudaError_t e = tc_gemm_launch(p.bn, v.tmVa, v.tmVb, gV, h->stream);
-    if (e == cudaSuccess) e = gram_final_launch(p.GB, p.gb_count, p.slab, p.r, p.rp, p.Gfin, h->stream, skip);
+    if (e == cudaSuccess) e = gram_final_launch(p.GB, p.gb_count, p.slab, p.r, p.rp, p.Gfin, p.Gpart, p.gcnt, h->stream, skip);
     if (e != cudaSuccess) return e;
     RowsParams q{};
     q.F = v.V;
@@ -729,7 +733,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
     }
     e = rows_update_launch(q, mode, h->stream);
     if (e == cudaSuccess) e = tc_gemm_launch(p.bn, v.tmWa, v.tmWb, gW, h->stream);
-    if (e == cudaSuccess) e = gram_final_launch(p.GD, v.gd_count, p.slab, p.r, p.rp, p.Gfin, h->stream, skip);
+    if (e == cudaSuccess) e = gram_final_launch(p.GD, v.gd_count, p.slab, p.r, p.rp, p.Gfin, p.Gpart, p.gcnt, h->stream, skip);
     if (e != cudaSuccess) return e;
     q.F = p.Wt;
     q.rows = p.n;
@@ -898,6 +902,7 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
+    if (p.gcnt) CK(cudaMemsetAsync(p.gcnt, 0, sizeof(int) * ceil_div(p.slab, 256), h->stream));
     CK(cudaMemcpyAsync(h->h_bad, p.d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
 
     // the whole hierarchy + schedule as one cached CUDA graph
@@ -1007,6 +1012,7 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
         Plan& p = plans[i];
         CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
         CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
+        if (p.gcnt) CK(cudaMemsetAsync(p.gcnt, 0, sizeof(int) * ceil_div(p.slab, 256), h->stream));
         CK(cudaMemsetAsync(p.conv_state, 0, 3 * sizeof(double), h->stream));
         CK(cudaMemsetAsync(p.conv_flag, 0, sizeof(int), h->stream));
         CK(cudaMemsetAsync(p.conv_count, 0, sizeof(long long), h->stream));
@@ -1383,6 +1389,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
+    if (p.gcnt) CK(cudaMemsetAsync(p.gcnt, 0, sizeof(int) * ceil_div(p.slab, 256), h->stream));
     KL(1, gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream));
     const Level& v = p.lv[0];
     const int mode = algo == NMF_HALS ? kModeHals : (algo == NMF_MU ? kModeMu : kModeStore);
@@ -1411,7 +1418,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                               : tc_gemm_launch(p.bn, v.tmWa, v.tmWb, v.gW, h->stream);
                 } else {
                     e = gram_final_launch(vstep ? p.GB : p.GD, vstep ? p.gb_count : v.gd_count, p.slab, p.r, p.rp,
-                                          p.Gfin, h->stream);
+                                          p.Gfin, p.Gpart, p.gcnt, h->stream);
                     RowsParams q{};
                     q.F = vstep ? v.V : p.Wt;
                     q.rows = vstep ? v.m : p.n;

@@ -26,7 +26,7 @@ namespace {
 
 constexpr int TM_ROWS = 128;          // MMA M
 constexpr int KB = 64;                // K columns per stage (128 bytes of bf16)
-constexpr int NSTAGE = 6;
+constexpr int NSTAGE = 4;  // two CTAs per SM (about 99 KB of shared memory each)
 constexpr int A_STAGE = TM_ROWS * KB * 2;  // 16 KiB
 
 __device__ __forceinline__ uint32_t elect_lane0() { return (threadIdx.x & 31) == 0; }
@@ -80,7 +80,7 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcGemmParams p) {
     constexpr int B_STAGE = BN * KB * 2;

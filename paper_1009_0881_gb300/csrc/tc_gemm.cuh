@@ -35,9 +35,13 @@ cudaError_t make_tmap_bf16_sw128(CUtensorMap* map, const __nv_bfloat16* base, ui
 // out[r*ldo + c] = bf16(in[r*ldi + c]) (transpose = false) or out[c*ldo + r] (true)
 cudaError_t to_bf16_launch(const float* in, int64_t ldi, int64_t rows, int64_t cols, __nv_bfloat16* out,
                            int64_t ldo, bool transpose, cudaStream_t st);
-// G[e] = sum over `count` slabs (stride `stride`) of slab[e], e < r * rp, fixed order
-cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int r, int rp, float* G,
-                              cudaStream_t st, const int* skip = nullptr);
+// G[e] = sum over `count` slabs (stride `stride`) of slab[e], e < r * rp, in a fixed order:
+// up to kGramChunks chunk sums (scratch `part`, kGramChunks * r * rp floats) added in chunk
+// order.  `cnt` holds ceil(r * rp / 256) ints, zero before the first launch (each launch
+// leaves them zero).
+constexpr int kGramChunks = 32;
+cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int r, int rp, float* G, float* part,
+                              int* cnt, cudaStream_t st, const int* skip = nullptr);
 
 struct RowsParams {
     float* F;              // rows x rp factor (FP32), updated in place
