@@ -81,7 +81,7 @@ __host__ __device__ inline Smem smem_layout(int br, int BA, int r, int rp, int c
     s.ared = o; o = align_up(o + sizeof(float) * R * kMaxRank, 128);
     s.fn = o;   o = align_up(o + sizeof(float) * R * kMaxRank, 128);
     s.dn = o;   o = align_up(o + sizeof(float) * R * kMaxRank, 128);
-    s.fg = o;   o = align_up(o + sizeof(float) * r * rp, 128);
+    s.fg = o;   o = align_up(o + sizeof(float4) * (size_t)cs * S4, 128);
     s.bar = o;  o = align_up(o + sizeof(uint64_t) * NST, 128);
     s.total = o;
     return s;
@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(NT, 1)
     ptx::grid_dependency_wait();
     ptx::launch_dependents();
     if (p.skip && *(volatile const int*)p.skip) return;  // same value in every CTA of the grid
+    ptx::cluster_arrive_relaxed();                       // matched by the wait before the first push
     if (tid == 0) {
         for (int s = 0; s < NST && s < nst; ++s) {
             if (!early_x) {
@@ -262,10 +263,21 @@ __global__ void __launch_bounds__(NT, 1)
             ptx::tma_load_2d(Ys + slot * KS * BR, &tmY, &bar[slot], 0, (int)(k0 + (s + NST) * KS));
         }
     }
+    ptx::cluster_wait();  // every CTA of the cluster has started: its shared memory may be written
+    // push the partial tile rows to the rank that reduces them: row a of the tile
+    // belongs to rank a / R, which receives the cs partials at Pt[(c R + a % R) BR + col]
 #pragma unroll
-    for (int i = 0; i < TM; ++i)
+    for (int i = 0; i < TM; ++i) {
+        const int a = ty * TM + i;
+        const int owner = a / R;
+        float* dst = cluster.map_shared_rank(Pt, owner) + (crank * R + (a - owner * R)) * BR + tx * TN;
+        if (TN == 4) {
+            *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1 % TN], acc[i][2 % TN], acc[i][3 % TN]);
+        } else {
 #pragma unroll
-        for (int j = 0; j < TN; ++j) Pt[(ty * TM + i) * BR + tx * TN + j] = acc[i][j];
+            for (int j = 0; j < TN; ++j) dst[j] = acc[i][j];
+        }
+    }
     if (!ok) atomicExch(p.err_flag, 1);
     ptx::cp_async_wait_all();
     __syncthreads();
@@ -276,30 +288,28 @@ __global__ void __launch_bounds__(NT, 1)
             for (int q = 0; q < p.gin_count; ++q) s = f4add(s, Gst[q * S4 + j]);
             Gsl[j] = s;
         }
+        __syncthreads();
+    }
+    // push this rank's Gram slice into the full Gram matrix of every rank
+    {
+        const int n4 = max(0, min(S4, F4 - crank * S4));
+        for (int t = tid; t < n4 * cs; t += NT) {
+            const int c = t / n4, j = t - c * n4;
+            reinterpret_cast<float4*>(cluster.map_shared_rank(Gs, c))[crank * S4 + j] = Gsl[j];
+        }
     }
 
-    cluster.sync();  // #1: partial tiles and Gram slices visible cluster-wide
+    cluster.sync();  // #1: partial tiles and Gram slices delivered to their ranks
 
-    // ---- full Gram (r x rp) from the slices of all ranks
-    for (int idx = tid; idx < F4; idx += NT) {
-        const int owner = idx / S4;
-        const float4* src = cluster.map_shared_rank(Gsl, owner);
-        reinterpret_cast<float4*>(Gs)[idx] = src[idx - owner * S4];
-    }
-    // ---- this CTA's R rows of the tile: sum of the cs partial tiles, fixed order
+    // ---- this CTA's R rows of the tile: sum of the cs partial tiles in rank order
     const int row0 = crank * R;
     const int Q4 = rp / 4;
-    cluster_sum_f4(
-        R * Q4, cs,
-        [&](int c, int e) {
-            const int rr = e / Q4, k4 = e - rr * Q4;
-            return *reinterpret_cast<const float4*>(cluster.map_shared_rank(Pt, c) + (row0 + rr) * BR + 4 * k4);
-        },
-        [&](int e, float4 s) {
-            const int rr = e / Q4, k4 = e - rr * Q4;
-            *reinterpret_cast<float4*>(Ared + rr * kMaxRank + 4 * k4) = s;
-        },
-        Part);
+    for (int e = tid; e < R * Q4; e += NT) {
+        const int rr = e / Q4, k4 = e - rr * Q4;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < cs; ++c) s = f4add(s, *reinterpret_cast<const float4*>(Pt + (c * R + rr) * BR + 4 * k4));
+        *reinterpret_cast<float4*>(Ared + rr * kMaxRank + 4 * k4) = s;
+    }
     __syncthreads();
     for (int k = tid; k < kMaxRank; k += NT) Ginv[k] = (k < r && Gs[k * rp + k] > 0.f) ? 1.f / Gs[k * rp + k] : 0.f;
     __syncthreads();
@@ -333,29 +343,31 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) ga[i][j] = fmaf(uu[i], vv[j], ga[i][j]);
             }
+            // push to the rank that owns this slice of the slab (Fg there holds cs partials)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int l = ty * 4 + i;
-                if (l < r && tx * 4 < rp)
-                    *reinterpret_cast<float4*>(Fg + l * rp + tx * 4) = make_float4(ga[i][0], ga[i][1], ga[i][2], ga[i][3]);
+                if (l < r && tx * 4 < rp) {
+                    const int idx = (l * rp + tx * 4) / 4;
+                    const int owner = idx / S4;
+                    reinterpret_cast<float4*>(cluster.map_shared_rank(Fg, owner))[crank * S4 + idx - owner * S4] =
+                        make_float4(ga[i][0], ga[i][1], ga[i][2], ga[i][3]);
+                }
             }
         }
-    }
 
-    cluster.sync();  // #3: Fg of every rank ready; remote reads of Pt and Gsl done
+        cluster.sync();  // #3: every rank's slab partials delivered
 
-    if (MODE != kModeStore) {
+        // this rank's slice of the tile's Gram slab: sum of the cs partials in rank order.
+        // Nothing reads another rank's shared memory after #3, so no closing barrier.
         float4* gout = reinterpret_cast<float4*>(p.Gout + (int64_t)tile * p.gout_stride);
         const int n4 = max(0, min(S4, F4 - crank * S4));
-        cluster_sum_f4(
-            n4, cs,
-            [&](int c, int j) {
-                return reinterpret_cast<const float4*>(cluster.map_shared_rank(Fg, c))[crank * S4 + j];
-            },
-            [&](int j, float4 s) { gout[crank * S4 + j] = s; }, Part);
+        for (int j = tid; j < n4; j += NT) {
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < cs; ++c) s = f4add(s, reinterpret_cast<const float4*>(Fg)[c * S4 + j]);
+            gout[crank * S4 + j] = s;
+        }
     }
-
-    cluster.sync();  // #4: keep this CTA's shared memory alive until all remote reads are done
 }
 
 // Partial Gram slabs of a tall factor: out[t] = F[bt t : bt t + bt]^T F[bt t : bt t + bt], bt <= 64.

@@ -68,6 +68,14 @@ __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepco
 // to start its prologue.
 __device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Split cluster barrier: every CTA arrives when it starts and waits before its
+// first access to another CTA's shared memory (all CTAs of the cluster have
+// then started).  Both are executed by all threads of the CTA.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
+
 // 2-D tiled TMA load of box (x, y) of `map` into shared memory, completing on `bar`.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
     asm volatile(
