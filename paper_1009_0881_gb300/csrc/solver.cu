@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -304,12 +305,15 @@ void layout(Plan& p, Bump& b, int num_sms) {
     p.tmp = b.take<float>((size_t)std::max<int64_t>(std::max<int64_t>(p.r * n, n * rp), p.lv[0].m * rp));
     p.slab = (int64_t)p.r * rp;
     p.gb_count = (int)ceil_div(n, p.wtile);
+    // slab buffers sized for the smallest tile height, so that the autotuner can try
+    // every candidate in place
+    const int min_tile = p.bf16 ? 64 : 16;
     int max_gd = 1;
     for (int l = 0; l < p.L; ++l) {
         p.lv[l].gd_count = (int)ceil_div(p.lv[l].m, p.lv[l].vtile);
-        max_gd = std::max(max_gd, p.lv[l].gd_count);
+        max_gd = std::max(max_gd, (int)ceil_div(p.lv[l].m, min_tile));
     }
-    p.GB = b.take<float>((size_t)(p.gb_count * p.slab));
+    p.GB = b.take<float>((size_t)(ceil_div(n, min_tile) * p.slab));
     p.GD = b.take<float>((size_t)(max_gd * p.slab));
     p.PA = b.take<float>((size_t)(p.lv[0].m * rp));
     p.PC = b.take<float>((size_t)(n * rp));
@@ -532,6 +536,122 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
 
 void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap);
 
+// ---------------------------------------------------------------------------
+// Autotuner of the half-sweep tile heights.  The planner's choice (choose_tile)
+// is a heuristic; the first time a shape is planned in the process each
+// candidate height (64, 32, 16 rows, with its cluster size) is timed on the
+// device with CUDA events over a few launches on the plan's own buffers, before
+// the problem is staged (the launches only read and write workspace that is
+// overwritten afterwards), and the fastest is kept for every later plan of that
+// shape.  The table is shared by all handles of the process, so a problem is
+// solved with the same tiles alone, in a batch or in the server.
+// NMF_TUNE=0 keeps the heuristic.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;  // "<V|W>:dev:rows:K:r" -> tile height
+
+std::string tune_key(char which, int dev, int64_t rows, int64_t K, int r) {
+    char b[96];
+    snprintf(b, sizeof b, "%c:%d:%lld:%lld:%d", which, dev, (long long)rows, (long long)K, r);
+    return b;
+}
+
+bool tune_enabled() {
+    const char* e = std::getenv("NMF_TUNE");
+    return !(e && e[0] == '0');
+}
+
+// Tiles already tuned for this shape (plan_dims applies them).
+void apply_tuned(nmf_ctx* h, Plan& p) {
+    if (p.bf16 || !tune_enabled()) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key('W', h->device, p.n, p.lv[0].m, p.r));
+    if (it != g_tune.end()) p.wtile = it->second;
+    for (int l = 0; l < p.L; ++l) {
+        it = g_tune.find(tune_key('V', h->device, p.lv[l].m, p.n, p.r));
+        if (it != g_tune.end()) p.lv[l].vtile = it->second;
+    }
+}
+
+// Mean time of `reps` launches of a half-sweep after one untimed launch (ms), or -1.
+float time_half_sweep(nmf_ctx* h, HalfSweepLaunch hl, int reps = 3) {
+    hl.mode = kModeHals;
+    hl.p.skip = nullptr;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return -1.f;
+    }
+    float ms = -1.f;
+    cudaError_t e = half_sweep_launch(hl, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) e = half_sweep_launch(hl, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        ms /= reps;
+    else
+        ms = -1.f, cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+int plan_half_sweeps(nmf_ctx* h, Plan& p);
+
+// Time the candidates of every untuned half-sweep of p and record the fastest.
+int tune_plan(nmf_ctx* h, Plan& p) {
+    if (p.bf16 || !tune_enabled()) return NMF_OK;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int cands[3] = {64, 32, 16};
+    auto pick = [&](char which, int64_t rows, auto set, auto launch_of) -> int {
+        const std::string key = tune_key(which, h->device, rows, which == 'W' ? p.lv[0].m : p.n, p.r);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            set(it->second);
+            return NMF_OK;
+        }
+        int best = -1;
+        float best_ms = 0.f;
+        for (int ba : cands) {
+            if (ceil_div(rows, ba) > active_clusters(h, p.br, ba, p.r)[0]) continue;
+            set(ba);
+            int rc = plan_half_sweeps(h, p);
+            if (rc) return rc;
+            const float ms = time_half_sweep(h, launch_of());
+            if (ms < 0.f) continue;
+            // a smaller tile must win by 3 % (it writes more Gram slabs)
+            if (best < 0 || ms < 0.97f * best_ms) {
+                best = ba;
+                best_ms = ms;
+            }
+        }
+        if (best < 0) best = 64;
+        set(best);
+        g_tune[key] = best;
+        return NMF_OK;
+    };
+    int rc = pick('W', p.n,
+                  [&](int ba) {
+                      p.wtile = ba;
+                      p.gb_count = (int)ceil_div(p.n, ba);
+                  },
+                  [&]() { return p.lv[0].hsW; });
+    if (rc) return rc;
+    for (int l = 0; l < p.L; ++l) {
+        rc = pick('V', p.lv[l].m,
+                  [&](int ba) {
+                      p.lv[l].vtile = ba;
+                      p.lv[l].gd_count = (int)ceil_div(p.lv[l].m, ba);
+                  },
+                  [&]() { return p.lv[l].hsV; });
+        if (rc) return rc;
+    }
+    return plan_half_sweeps(h, p);
+}
+
+
 // Plans of several problems laid out back to back in the handle's workspace.
 int make_plans(nmf_ctx* h, std::vector<Plan>& plans) {
     Bump dry;
@@ -545,6 +665,8 @@ int make_plans(nmf_ctx* h, std::vector<Plan>& plans) {
     for (Plan& p : plans) {
         layout(p, real, h->num_sms);
         rc = plan_half_sweeps(h, p);
+        if (rc) return rc;
+        rc = tune_plan(h, p);
         if (rc) return rc;
     }
     return NMF_OK;
@@ -568,7 +690,9 @@ int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, 
     real.base = h->ws;
     real.cap = h->ws_cap;
     layout(p, real, h->num_sms);
-    return plan_half_sweeps(h, p);
+    rc = plan_half_sweeps(h, p);
+    if (rc) return rc;
+    return tune_plan(h, p);
 }
 
 void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap) {
@@ -596,6 +720,7 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
     }
     for (int l = 0; l < L; ++l)
         p.lv[l].vtile = p.bf16 ? 64 : choose_tile(h, p.br, r, p.lv[l].m, nullptr);
+    apply_tuned(h, p);
 }
 
 // One sweep of the inner algorithm at level l: the V-step (products M W^T and
