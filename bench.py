@@ -54,6 +54,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-serving-form", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-rate-low", type=float, default=40.0)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--_oracle_sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -639,73 +640,84 @@ def batched_form(args, pool, reps=3):
 def serving_form(args, pool):
     """Poisson arrivals into nmf_server: sizes from the 64-problem pool, algorithm uniform over
     HALS/MU/ANLS, 40 GB workspace budget.  M stays on the device; each request brings its
-    initial V, W from host memory and gets the result back there."""
-    import numpy as np
+    initial V, W from host memory and gets the result back there.  Run at the configured
+    rate and again at a lower rate the server sustains (latency without a standing queue)."""
     import torch
 
-    from paper_1009_0881_gb300 import native, synth
+    from paper_1009_0881_gb300 import native
 
     Mds = [torch.from_numpy(p.M).cuda() for p in pool]
     torch.cuda.synchronize()
     algos = ("hals", "mu", "anls")
     budget = 40 * 10**9
-    out = {"rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "slots": args.serve_slots,
-           "hbm_budget_bytes": budget, "levels": BATCH_LEVELS, "iters_cap": SERVE_ITERS, "rel_tol": BATCH_TOL,
-           "sizes": "uniform over the 64 seeded batched-form problems"}
-    n_req = int(args.serve_rate * args.serve_seconds * 1.5) + 16
-    gaps = synth.exponential(7, 11, n_req) / args.serve_rate
-    pick = synth.uniform(7, 12, n_req)
+    out = {"rate_per_s": args.serve_rate, "low_rate_per_s": args.serve_rate_low, "seconds": args.serve_seconds,
+           "slots": args.serve_slots, "hbm_budget_bytes": budget, "levels": BATCH_LEVELS, "iters_cap": SERVE_ITERS,
+           "rel_tol": BATCH_TOL, "sizes": "uniform over the 64 seeded batched-form problems",
+           "latency": "from nmf_server_submit to completion"}
     for label, prec in (("fp32", native.NMF_FP32), ("bf16", native.NMF_BF16)):
         with native.Server(0, hbm_budget_bytes=budget, slots=args.serve_slots, precision=prec) as srv:
             # warm-up: every (problem, algorithm) once, so the slots' graphs and workspaces exist
             t0 = time.perf_counter()
             tickets = [srv.submit(_request(p, Md, a, iters=SERVE_ITERS)) for p, Md in zip(pool, Mds) for a in algos]
             warm = [srv.poll(t, -1) for t in tickets]
-            warm_s = time.perf_counter() - t0
-            lat, outstanding, status, by_algo, held = [], {}, [], {a: 0 for a in algos}, 0
-            t_start = time.perf_counter()
-            t_next = t_start
-            i = 0
-            t_end = t_start + args.serve_seconds
-
-            def drain(wait):
-                for t in list(outstanding):
-                    r = srv.poll(t, wait)
-                    if r is not None:
-                        status.append(r[0])
-                        lat.append(r[3])
-                        del outstanding[t]
-
-            while True:
-                now = time.perf_counter()
-                if now >= t_end or i + 1 >= n_req:
-                    break
-                if now >= t_next:
-                    k = min(int(pick[i] * 3 * len(pool)), 3 * len(pool) - 1)
-                    a = algos[k % 3]
-                    p, Md = pool[k // 3], Mds[k // 3]
-                    outstanding[srv.submit(_request(p, Md, a, iters=SERVE_ITERS))] = a
-                    by_algo[a] += 1
-                    i += 1
-                    t_next += gaps[i]
-                    continue
-                drain(0)
-                held = max(held, srv.stats()["bytes_held"])
-                time.sleep(min(max(t_next - time.perf_counter(), 0.0), 0.001))
-            submitted = i
-            drain(-1)
-            wall = time.perf_counter() - t_start
-            lat_a = np.array(lat)
-            out[label] = {"submitted": submitted, "completed": len(lat), "all_ok": all(s == 0 for s in status),
-                          "solves_per_s": len(lat) / wall, "wall_s": wall,
-                          "latency_ms": {"p50": float(np.percentile(lat_a, 50)), "p99": float(np.percentile(lat_a, 99)),
-                                         "mean": float(lat_a.mean()), "max": float(lat_a.max())},
-                          "per_algo_requests": by_algo, "max_bytes_held": held, "warmup_s": warm_s,
-                          "warmup_ok": all(w[0] == 0 for w in warm)}
+            res = {"warmup_s": time.perf_counter() - t0, "warmup_ok": all(w[0] == 0 for w in warm)}
+            res["offered"] = _poisson_run(srv, pool, Mds, args.serve_rate, args.serve_seconds, seed=7)
+            res["low_rate"] = _poisson_run(srv, pool, Mds, args.serve_rate_low, args.serve_seconds, seed=8)
+            out[label] = res
     del Mds
     torch.cuda.empty_cache()
     return out
 
+
+def _poisson_run(srv, pool, Mds, rate, seconds, seed):
+    """Submit Poisson arrivals at `rate` for `seconds`, then drain; latency and throughput."""
+    import numpy as np
+
+    from paper_1009_0881_gb300 import synth
+
+    algos = ("hals", "mu", "anls")
+    n_req = int(rate * seconds * 1.5) + 16
+    gaps = synth.exponential(seed, 11, n_req) / rate
+    pick = synth.uniform(seed, 12, n_req)
+    lat, outstanding, status, by_algo, held = [], {}, [], {a: 0 for a in algos}, 0
+    t_start = time.perf_counter()
+    t_next = t_start
+    t_end = t_start + seconds
+    i = 0
+
+    def drain(wait):
+        for t in list(outstanding):
+            r = srv.poll(t, wait)
+            if r is not None:
+                status.append(r[0])
+                lat.append(r[3])
+                del outstanding[t]
+
+    while True:
+        now = time.perf_counter()
+        if now >= t_end or i + 1 >= n_req:
+            break
+        if now >= t_next:
+            k = min(int(pick[i] * 3 * len(pool)), 3 * len(pool) - 1)
+            a = algos[k % 3]
+            p, Md = pool[k // 3], Mds[k // 3]
+            outstanding[srv.submit(_request(p, Md, a, iters=SERVE_ITERS))] = a
+            by_algo[a] += 1
+            i += 1
+            t_next += gaps[i]
+            continue
+        drain(0)
+        held = max(held, srv.stats()["bytes_held"])
+        time.sleep(min(max(t_next - time.perf_counter(), 0.0), 0.001))
+    submitted = i
+    drain(-1)
+    wall = time.perf_counter() - t_start
+    lat_a = np.array(lat)
+    return {"rate_per_s": rate, "submitted": submitted, "completed": len(lat), "all_ok": all(x == 0 for x in status),
+            "solves_per_s": len(lat) / wall, "wall_s": wall,
+            "latency_ms": {"p50": float(np.percentile(lat_a, 50)), "p99": float(np.percentile(lat_a, 99)),
+                           "mean": float(lat_a.mean()), "max": float(lat_a.max())},
+            "per_algo_requests": by_algo, "max_bytes_held": held}
 
 if __name__ == "__main__":
     a = parse_args()
