@@ -86,6 +86,42 @@ __device__ __forceinline__ void rows_times_gram(int R, int r, int rp, const floa
     }
 }
 
+// Dn = Fn G for up to 16 rows at a time with the thread's row of Fn held in
+// registers (one shared-memory load of G per column group and l, no dependent
+// load of Fn inside the l loop); thread (ty, tx) computes columns 4tx .. 4tx+3 of
+// row ty.  Same summation order as rows_times_gram.
+__device__ __forceinline__ void rows_times_gram_reg(int R, int r, int rp, const float* Fn, const float* Gs, float* Dn) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int c0 = 4 * tx;
+    for (int rb = 0; rb < R; rb += 16) {
+        const int rr = rb + ty;
+        float f[kMaxRank];
+#pragma unroll
+        for (int q = 0; q < kMaxRank / 4; ++q) {
+            const float4 v = rr < R ? *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + 4 * q)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            f[4 * q] = v.x;
+            f[4 * q + 1] = v.y;
+            f[4 * q + 2] = v.z;
+            f[4 * q + 3] = v.w;
+        }
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (c0 < rp) {
+#pragma unroll
+            for (int l = 0; l < kMaxRank; ++l) {
+                if (l < r) {
+                    const float4 gv = *reinterpret_cast<const float4*>(Gs + l * rp + c0);
+                    a0 = fmaf(f[l], gv.x, a0);
+                    a1 = fmaf(f[l], gv.y, a1);
+                    a2 = fmaf(f[l], gv.z, a2);
+                    a3 = fmaf(f[l], gv.w, a3);
+                }
+            }
+        }
+        if (rr < R) *reinterpret_cast<float4*>(Dn + rr * kMaxRank + c0) = make_float4(a0, a1, a2, a3);
+    }
+}
+
 // The same product for few rows: S consecutive lanes share one group of four
 // outputs, lane s summing l = s, s + S, ..., and the S partial sums are combined
 // by butterfly shuffles.  Requires R * (rp/4) * S <= NT.
@@ -128,7 +164,7 @@ __device__ __forceinline__ void rows_times_gram_any(int R, int r, int rp, const 
     else if (groups * 2 <= NT)
         rows_times_gram_split<2>(R, r, rp, Fn, Gs, Dn);
     else if (R <= 16)
-        rows_times_gram<1>(R, r, rp, Fn, Gs, Dn);
+        rows_times_gram_reg(R, r, rp, Fn, Gs, Dn);
     else if (R <= 32)
         rows_times_gram<2>(R, r, rp, Fn, Gs, Dn);
     else
@@ -236,12 +272,94 @@ __device__ __forceinline__ void update_rows(float* __restrict__ F, int Na, int r
 }
 
 
+// Update of R rows with a half-warp per row (two rows per warp at a time): the
+// same column walk as update_rows, lane s of the half owning entries 4s .. 4s+3.
+template <int MODE>
+__device__ __forceinline__ void update_rows_half(float* __restrict__ F, int Na, int r, int rp, int R, int64_t rowbase,
+                                                 float* Fn, const float* Ared, const float* Dn, const float* Gs,
+                                                 const float* Ginv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sl = lane & 15, half = lane >> 4;
+    const int c0 = 4 * sl;
+    const bool has = c0 < r;
+    for (int base = warp * 2; base < R; base += (NT / 32) * 2) {
+        const int rr = base + half;
+        const bool act = rr < R && rowbase + rr < Na;
+        float f[4], g[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = c0 + e;
+            const bool ok = act && k < r;
+            f[e] = ok ? Fn[rr * kMaxRank + k] : 0.f;
+            const float pv = ok ? Ared[rr * kMaxRank + k] : 0.f;
+            const float dv = ok ? Dn[rr * kMaxRank + k] : 0.f;
+            g[e] = MODE == kModeHals ? pv - dv : (ok ? f[e] * pv / fmaxf(dv, 1e-30f) : 0.f);
+        }
+        if (MODE == kModeHals) {
+            const int nchunks = (r + 3) / 4;
+            for (int t = 0; t < nchunks; ++t) {
+                float Gk[4][4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int kk = 4 * t + e;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (kk < r && c0 < rp) v = *reinterpret_cast<const float4*>(Gs + kk * rp + c0);
+                    Gk[e][0] = v.x;
+                    Gk[e][1] = v.y;
+                    Gk[e][2] = v.z;
+                    Gk[e][3] = v.w;
+                }
+                const float4 gi4 = *reinterpret_cast<const float4*>(Ginv + 4 * t);
+                const float gi[4] = {gi4.x, gi4.y, gi4.z, gi4.w};
+                float gt[4] = {g[0], g[1], g[2], g[3]};
+                float ft[4] = {f[0], f[1], f[2], f[3]};
+                float dl[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float nv = fmaxf(0.f, fmaf(gt[e], gi[e], ft[e]));
+                    dl[e] = nv - ft[e];
+                    ft[e] = nv;
+#pragma unroll
+                    for (int e2 = e + 1; e2 < 4; ++e2) gt[e2] = fmaf(-dl[e], Gk[e][e2], gt[e2]);
+                }
+                float d[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) d[e] = __shfl_sync(kFull, dl[e], t, 16);
+                const bool own = sl == t;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    f[j] = own ? ft[j] : f[j];
+                    float gj = g[j];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) gj = fmaf(-d[e], Gk[e][j], gj);
+                    g[j] = gj;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) f[e] = g[e];
+        }
+        if (rr < R)
+            *reinterpret_cast<float4*>(Fn + rr * kMaxRank + c0) =
+                act ? make_float4(f[0], f[1], f[2], f[3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act && has) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (c0 + e < r) F[(rowbase + rr) * rp + c0 + e] = f[e];
+        }
+    }
+}
+
 // Dispatch of update_rows on the number of rows per warp: rows are interleaved
 // so that the eight warps of the CTA share the R rows.
 template <int MODE>
 __device__ __forceinline__ void update_rows_any(float* __restrict__ F, int Na, int r, int rp, int R, int64_t rowbase,
                                                 float* Fn, const float* Ared, const float* Dn, const float* Gs,
                                                 const float* Ginv) {
+    if (R > 8 && R <= 16) {
+        update_rows_half<MODE>(F, Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv);
+        return;
+    }
     const int rpw = R <= 8 ? 1 : (R <= 16 ? 2 : (R <= 32 ? 4 : 8));
     switch (rpw) {
         case 1: update_rows<1, MODE>(F, Na, r, rp, R, rowbase, Fn, Ared, Dn, Gs, Ginv); break;
