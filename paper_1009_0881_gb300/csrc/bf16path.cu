@@ -80,37 +80,68 @@ __global__ void gram_final_kernel(const float* __restrict__ slabs, int count, in
 
 constexpr int TLD = BA + 1;  // row stride of the transposed tiles (odd: conflict-free columns)
 
-// HALS update (Algorithm HALS) of the BA rows of a tile, one thread per row:
-// the thread keeps g = P_i - F_i G of its row in registers and walks the
-// columns k = 0 .. r-1 in order, F_ik <- max(0, F_ik + g_k / G_kk), then
-// g_j -= delta G_kj for the later columns j.  The register array is shifted
-// by one column per step (g[0] is always the current g_k), so the loop over k
-// stays rolled (compact code) while every register index is static; Gsk holds
-// row k of G shifted the same way, Gsk[k][j] = G[k][k+1+j] (zero past r).
-// FT / GT hold F and g transposed (column k of the tile at FT + k * TLD).
-template <int RB>
-__device__ __forceinline__ void hals_rows_lane(int r, float* FT, const float* GT, const float* Gsk, const float* Ginv) {
-    const int rr = threadIdx.x;
-    if (rr >= BA) return;
-    float g[RB];
+// HALS update (Algorithm HALS) of the BA = 64 rows of a tile, four lanes per row
+// (all 256 threads busy): lane q of a row's quad holds columns 16q .. 16q+15 of
+// F_i and of g = P_i - F_i G in registers.  Columns k = 0 .. r-1 are walked in
+// order: the owner lane of column k computes F_ik <- max(0, F_ik + g_k / G_kk)
+// and broadcasts the change d within the quad, then every lane applies
+// g_j -= d G_kj to its sixteen columns (those at or before k are finished and
+// no longer read).  G64 is G zero-padded to 64 x 64; the loop over k is fully
+// unrolled so that every register index is static.  New rows go back to Fn
+// (row-major) and FT (transposed, for the BF16 copy).
+__device__ __forceinline__ void hals_rows_quad(int r, int rp, float* Fn, const float* Ared, const float* Dn,
+                                               float* FT, const float* G64, const float* Ginv) {
+    const int tid = threadIdx.x;
+    const int rr = tid >> 2, qd = tid & 3;
+    const int gbase = (tid & 31) & ~3;
+    float f[16], g[16];
 #pragma unroll
-    for (int k = 0; k < RB; ++k) g[k] = GT[k * TLD + rr];
-#pragma unroll 1
-    for (int k = 0; k < r; ++k) {
-        const float fk = FT[k * TLD + rr];
-        const float nv = fmaxf(0.f, fmaf(g[0], Ginv[k], fk));
-        const float d = nv - fk;
-        FT[k * TLD + rr] = nv;
-        const float4* gk = reinterpret_cast<const float4*>(Gsk + k * kMaxRank);
+    for (int v = 0; v < 4; ++v) {
+        const int c = 16 * qd + 4 * v;
+        const float4 fv = *reinterpret_cast<const float4*>(Fn + rr * kMaxRank + c);
+        float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < rp) {
+            const float4 av = *reinterpret_cast<const float4*>(Ared + rr * kMaxRank + c);
+            const float4 dv = *reinterpret_cast<const float4*>(Dn + rr * kMaxRank + c);
+            gv = make_float4(av.x - dv.x, av.y - dv.y, av.z - dv.z, av.w - dv.w);
+        }
+        f[4 * v] = fv.x;
+        f[4 * v + 1] = fv.y;
+        f[4 * v + 2] = fv.z;
+        f[4 * v + 3] = fv.w;
+        g[4 * v] = gv.x;
+        g[4 * v + 1] = gv.y;
+        g[4 * v + 2] = gv.z;
+        g[4 * v + 3] = gv.w;
+    }
 #pragma unroll
-        for (int q = 0; q < RB / 4; ++q) {
-            const float4 gv = gk[q];
-            g[4 * q + 0] = fmaf(-d, gv.x, g[4 * q + 1]);
-            g[4 * q + 1] = fmaf(-d, gv.y, g[4 * q + 2]);
-            g[4 * q + 2] = fmaf(-d, gv.z, g[4 * q + 3]);
-            g[4 * q + 3] = 4 * q + 4 < RB ? fmaf(-d, gv.w, g[(4 * q + 4) % RB]) : 0.f;
+    for (int k = 0; k < kMaxRank; ++k) {
+        if (k < r) {
+            const int q0 = k >> 4, i0 = k & 15;
+            float dl = 0.f;
+            if (qd == q0) {
+                const float nv = fmaxf(0.f, fmaf(g[i0], Ginv[k], f[i0]));
+                dl = nv - f[i0];
+                f[i0] = nv;
+            }
+            const float d = __shfl_sync(0xffffffffu, dl, gbase + q0);
+            const float4* gk = reinterpret_cast<const float4*>(G64 + k * kMaxRank + 16 * qd);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float4 gv = gk[v];
+                g[4 * v] = fmaf(-d, gv.x, g[4 * v]);
+                g[4 * v + 1] = fmaf(-d, gv.y, g[4 * v + 1]);
+                g[4 * v + 2] = fmaf(-d, gv.z, g[4 * v + 2]);
+                g[4 * v + 3] = fmaf(-d, gv.w, g[4 * v + 3]);
+            }
         }
     }
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        *reinterpret_cast<float4*>(Fn + rr * kMaxRank + 16 * qd + 4 * v) =
+            make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) FT[(16 * qd + j) * TLD + rr] = f[j];
 }
 
 template <int MODE>
@@ -124,9 +155,8 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
     float* Ared = Fn + BA * kMaxRank;     // BA x kMaxRank
     float* Dn = Ared + BA * kMaxRank;     // BA x kMaxRank
     float* Fg = Dn + BA * kMaxRank;       // r x rp
-    float* FT = Fg + r * rp;              // kMaxRank x TLD (HALS: F transposed)
-    float* GT = FT + kMaxRank * TLD;      // kMaxRank x TLD (HALS: g transposed)
-    float* G64 = GT + kMaxRank * TLD;     // kMaxRank x kMaxRank (HALS: shifted rows of G, see hals_rows_lane)
+    float* FT = Fg + r * rp;              // kMaxRank x TLD (HALS: new rows transposed)
+    float* G64 = FT + kMaxRank * TLD;     // kMaxRank x kMaxRank (HALS: G zero-padded)
     const int tid = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * BA;
     const int R = BA;
@@ -167,32 +197,14 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
         rowupd::rows_times_gram<4>(R, r, rp, Fn, Gs, Dn);
         __syncthreads();
         if (MODE == rowupd::kModeHals) {
-            // transposed F and g = P - F G (zero past rp), zero-padded G
-            for (int e = tid; e < BA * kMaxRank; e += NT) {
-                const int rr = e / kMaxRank, k = e - rr * kMaxRank;
-                FT[k * TLD + rr] = Fn[e];
-                GT[k * TLD + rr] = k < rp ? Ared[e] - Dn[e] : 0.f;
-            }
             for (int e = tid; e < kMaxRank * kMaxRank; e += NT) {
-                const int k = e / kMaxRank, j = k + 1 + (e - k * kMaxRank);
+                const int k = e / kMaxRank, j = e - k * kMaxRank;
                 G64[e] = (k < r && j < r) ? Gs[k * rp + j] : 0.f;
             }
             __syncthreads();
-            if (r <= 16)
-                hals_rows_lane<16>(r, FT, GT, G64, Ginv);
-            else if (r <= 32)
-                hals_rows_lane<32>(r, FT, GT, G64, Ginv);
-            else if (r <= 48)
-                hals_rows_lane<48>(r, FT, GT, G64, Ginv);
-            else
-                hals_rows_lane<64>(r, FT, GT, G64, Ginv);
+            hals_rows_quad(r, rp, Fn, Ared, Dn, FT, G64, Ginv);
             __syncthreads();
-            // new rows back to row-major, and to the factor in global memory
-            for (int e = tid; e < BA * kMaxRank; e += NT) {
-                const int rr = e / kMaxRank, k = e - rr * kMaxRank;
-                Fn[e] = FT[k * TLD + rr];
-            }
-            __syncthreads();
+            // new rows to the factor in global memory
             for (int e = tid; e < BA * Q4; e += NT) {
                 const int rr = e / Q4, k4 = e - rr * Q4;
                 const int64_t row = row0 + rr;
@@ -247,7 +259,7 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
 }
 
 size_t rows_smem_bytes(int r, int rp) {
-    return sizeof(float) * ((size_t)2 * r * rp + kMaxRank + 3 * BA * kMaxRank + 2 * kMaxRank * TLD +
+    return sizeof(float) * ((size_t)2 * r * rp + kMaxRank + 3 * BA * kMaxRank + kMaxRank * TLD +
                             kMaxRank * kMaxRank);
 }
 
