@@ -74,8 +74,6 @@ struct UpdateArgs {
     double* Gd;        // ANLS: r x r scratch receiving the FP64 sum of the Gram partials
 };
 
-cudaError_t hals_update_launch(const UpdateArgs& a, int num_sms, cudaStream_t st);
-cudaError_t mu_update_launch(const UpdateArgs& a, int num_sms, cudaStream_t st);
 // ANLS: F rows = argmin_{x>=0} 1/2 x^T G x - p^T x, FP64 active set.  status: device int
 // (0 ok, 1 iteration cap hit) OR-ed over all rows.
 cudaError_t anls_update_launch(const UpdateArgs& a, int num_sms, int* d_status, cudaStream_t st);

@@ -1,157 +1,18 @@
-// Row-parallel factor updates of the three inner NMF algorithms.
+// ANLS factor update (Algorithm ANLS, Section 2.1; Appendix A.2).
 //
 // The V-step updates the rows of V from (A = M W^T, B = W W^T); the W-step
-// updates the rows of Wt = W^T from (C^T = M^T V, D = V^T V).  Both steps act
-// on independent rows of a tall factor F with an r x r Gram matrix G, so one
-// kernel serves both.  Products arrive as split-K partial slabs and are summed
-// here in a fixed order (deterministic results).
-//
-// HALS (Algorithm HALS, Section 2.3).  Row i of F is updated column by column,
-// k = 1..r, in Gauss-Seidel order:
-//     F_ik <- max(0, (P_ik - sum_{l != k} F_il G_lk) / G_kk).
-// With g = P_i - F_i G kept up to date, the same value is F_ik + g_k / G_kk, and
-// after F_ik moves by delta every g_j drops by delta * G_kj.  The sequential
-// chain is then one division and one broadcast per k; the r-long dot products
-// of the formula become r independent FMAs spread over the lanes.
-// A group of 8 lanes owns one row (lane s holds entries k = s, s+8, ...), so a
-// warp updates 4 rows at once; G lives in shared memory.
-//
-// MU (Algorithm MU, Section 2.2): F <- F o P / max(F G, 1e-30), entrywise.
-//
-// ANLS (Algorithm ANLS, Section 2.1; Appendix A.2): each row solves
+// updates the rows of Wt = W^T from (C^T = M^T V, D = V^T V).  Each row solves
 //     min_{x >= 0} 1/2 x^T G x - P_i x
-// by the Lawson-Hanson active-set method in FP64 (Gram, right-hand side and
-// Cholesky factorisations of the passive block), one warp per row.
+// by the Lawson-Hanson active-set method in FP64, one warp per row, with the
+// Cholesky factor of the passive block grown column by column (HALS and MU are
+// updated inside the fused half-sweep kernel and the BF16 row kernel).
 #include "nmf_internal.cuh"
 
 namespace nmfk {
 
 namespace {
 
-constexpr int kLanesPerRow = 8;
-constexpr int kSlots = kMaxRank / kLanesPerRow;  // entries per lane
 constexpr unsigned kFull = 0xffffffffu;
-constexpr float kMuEps = 1e-30f;
-
-// Sum the Gram partial slabs into shared memory (row-major r x r).
-template <typename T>
-__device__ void reduce_gram(const UpdateArgs& u, T* G) {
-    const int r = u.r;
-    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
-        const int l = idx / r, k = idx - l * r;
-        const float* p = u.PG + (int64_t)l * u.ldpg + k;
-        T s = 0;
-        for (int q = 0; q < u.gsplits; ++q) s += (T)p[(int64_t)q * u.pgs];
-        G[idx] = s;
-    }
-    __syncthreads();
-}
-
-template <bool kHals>
-__global__ void __launch_bounds__(256) rows_update_kernel(const UpdateArgs u) {
-    extern __shared__ float Gs[];
-    reduce_gram<float>(u, Gs);
-    const int r = u.r;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane & (kLanesPerRow - 1);
-    const int gbase = lane & ~(kLanesPerRow - 1);
-    const int warp = threadIdx.x >> 5;
-    const int warps = blockDim.x >> 5;
-    const int rows_per_warp = 32 / kLanesPerRow;
-
-    for (int64_t base = ((int64_t)blockIdx.x * warps + warp) * rows_per_warp; base < u.rows;
-         base += (int64_t)gridDim.x * warps * rows_per_warp) {
-        const int64_t row = base + (lane / kLanesPerRow);
-        const bool active = row < u.rows;
-        float f[kSlots], g[kSlots];
-#pragma unroll
-        for (int j = 0; j < kSlots; ++j) {
-            const int k = sub + kLanesPerRow * j;
-            f[j] = 0.f;
-            g[j] = 0.f;
-            if (active && k < r) {
-                f[j] = u.F[row * u.ldf + k];
-                const float* p = u.P + row * u.ldp + k;
-                float s = 0.f;
-                for (int q = 0; q < u.splits; ++q) s += p[(int64_t)q * u.ps];
-                g[j] = s;
-            }
-        }
-        // den = F_i G (all l, current values)
-        float den[kSlots];
-#pragma unroll
-        for (int j = 0; j < kSlots; ++j) den[j] = 0.f;
-#pragma unroll
-        for (int jl = 0; jl < kSlots; ++jl) {
-#pragma unroll
-            for (int src = 0; src < kLanesPerRow; ++src) {
-                const int l = src + kLanesPerRow * jl;
-                if (l < r) {
-                    const float fl = __shfl_sync(kFull, f[jl], gbase + src);
-                    const float* Gl = Gs + l * r;
-#pragma unroll
-                    for (int j = 0; j < kSlots; ++j) {
-                        const int k = sub + kLanesPerRow * j;
-                        if (k < r) den[j] = fmaf(fl, Gl[k], den[j]);
-                    }
-                }
-            }
-        }
-        if (kHals) {
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j) g[j] -= den[j];
-            // Gauss-Seidel over k = 0..r-1
-#pragma unroll
-            for (int jk = 0; jk < kSlots; ++jk) {
-#pragma unroll
-                for (int src = 0; src < kLanesPerRow; ++src) {
-                    const int k = src + kLanesPerRow * jk;
-                    if (k < r) {
-                        const float gkk = Gs[k * r + k];
-                        float delta = 0.f;
-                        if (sub == src && gkk > 0.f) {
-                            const float nv = fmaxf(0.f, f[jk] + g[jk] / gkk);
-                            delta = nv - f[jk];
-                            f[jk] = nv;
-                        }
-                        delta = __shfl_sync(kFull, delta, gbase + src);
-                        const float* Gk = Gs + k * r;
-#pragma unroll
-                        for (int j = 0; j < kSlots; ++j) {
-                            const int kk = sub + kLanesPerRow * j;
-                            if (kk < r) g[j] = fmaf(-delta, Gk[kk], g[j]);
-                        }
-                    }
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j) f[j] = f[j] * g[j] / fmaxf(den[j], kMuEps);
-        }
-        if (active) {
-#pragma unroll
-            for (int j = 0; j < kSlots; ++j) {
-                const int k = sub + kLanesPerRow * j;
-                if (k < r) u.F[row * u.ldf + k] = f[j];
-            }
-        }
-    }
-}
-
-cudaError_t rows_update_launch(const UpdateArgs& u, int num_sms, bool hals, cudaStream_t st) {
-    if (u.rows <= 0) return cudaSuccess;
-    const int threads = 256;
-    const int64_t rows_per_cta = threads / kLanesPerRow;
-    int64_t grid = ceil_div(u.rows, rows_per_cta);
-    const int64_t cap = 4LL * num_sms;
-    if (grid > cap) grid = cap;
-    const size_t smem = sizeof(float) * u.r * u.r;
-    if (hals)
-        rows_update_kernel<true><<<(unsigned)grid, threads, smem, st>>>(u);
-    else
-        rows_update_kernel<false><<<(unsigned)grid, threads, smem, st>>>(u);
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // ANLS: warp-per-row Lawson-Hanson NNLS in FP64.
@@ -487,14 +348,6 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
 }
 
 }  // namespace
-
-cudaError_t hals_update_launch(const UpdateArgs& a, int num_sms, cudaStream_t st) {
-    return rows_update_launch(a, num_sms, true, st);
-}
-
-cudaError_t mu_update_launch(const UpdateArgs& a, int num_sms, cudaStream_t st) {
-    return rows_update_launch(a, num_sms, false, st);
-}
 
 static size_t anls_smem_bytes(int r) {
     return sizeof(double) * ((size_t)r * r + kAnlsWarps * anls_warp_doubles(r)) +
