@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(NT, 1)
     bool ok = true;
 
     if (tid == 0) {
+        ptx::prefetch_tmap(&tmX);
+        ptx::prefetch_tmap(&tmY);
         for (int s = 0; s < NST; ++s) ptx::mbar_init(&bar[s], 1);
         ptx::fence_mbar_init();
     }
