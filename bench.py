@@ -389,6 +389,8 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
         out["plain_fp32_single_level"] = plain
 
     out["roofline"], out["kernel_times_per_step_ms"] = roofline(args, h, Md, gh, gw, n, r, sched)
+    if args.workload == WORKLOAD:
+        out["other_algorithms"] = other_algorithms(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw)
     if not args.no_precision_form:
         out["precision_form"] = precision_form(args)
     if not (args.no_batched_form and args.no_serving_form):
@@ -423,6 +425,37 @@ def _traffic(kernel):
         with open(os.path.join(ROOT, "paper_1009_0881_gb300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return t["bytes"] if hsh.hexdigest()[:16] == t["src"] else None
+
+
+def other_algorithms(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw):
+    """MU and ANLS on the same workload, multilevel (L = 3) next to single-level, same sweep
+    budget; objective against the FP64 oracle's stored value where one exists."""
+    import torch
+
+    from paper_1009_0881_gb300 import native
+
+    out = {}
+    for algo in ("mu", "anls"):
+        for L in (3, 1):
+            sweeps = sum(native.schedule("vcycle", L, args.iters))
+            ms = []
+            for it in range(2):
+                Vd.copy_(V0d)
+                Wd.copy_(W0d)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=args.iters)
+                e1.record(stream)
+                e1.synchronize()
+                if it:
+                    ms.append(e0.elapsed_time(e1))
+            f = h.error(Md, Vd, Wd)
+            fstar = golden.get(f"grid19_{algo}_L{L}_K{args.iters}", {}).get("objective")
+            out[f"{algo}_L{L}"] = {"ms_per_solve": ms[0], "sweeps": sweeps, "sweeps_per_s": sweeps / (ms[0] / 1e3),
+                                   "objective": f, "oracle_fp64": fstar,
+                                   "rel_diff": None if fstar is None else abs(f - fstar) / fstar}
+    return out
 
 
 def _peaks():
