@@ -573,8 +573,8 @@ void apply_tuned(nmf_ctx* h, Plan& p) {
     }
 }
 
-// Mean time of `reps` launches of a half-sweep after one untimed launch (ms), or -1.
-float time_half_sweep(nmf_ctx* h, HalfSweepLaunch hl, int reps = 3) {
+// Mean time of `reps` launches of a half-sweep after two untimed launches (ms), or -1.
+float time_half_sweep(nmf_ctx* h, HalfSweepLaunch hl, int reps = 8) {
     hl.mode = kModeHals;
     hl.p.skip = nullptr;
     cudaEvent_t e0, e1;
@@ -585,6 +585,7 @@ float time_half_sweep(nmf_ctx* h, HalfSweepLaunch hl, int reps = 3) {
     }
     float ms = -1.f;
     cudaError_t e = half_sweep_launch(hl, h->stream);
+    if (e == cudaSuccess) e = half_sweep_launch(hl, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
     for (int i = 0; i < reps && e == cudaSuccess; ++i) e = half_sweep_launch(hl, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
@@ -605,34 +606,38 @@ int tune_plan(nmf_ctx* h, Plan& p) {
     if (p.bf16 || !tune_enabled()) return NMF_OK;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int cands[3] = {64, 32, 16};
-    auto pick = [&](char which, int64_t rows, auto set, auto launch_of) -> int {
+    auto pick = [&](char which, int64_t rows, int current, auto set, auto launch_of) -> int {
         const std::string key = tune_key(which, h->device, rows, which == 'W' ? p.lv[0].m : p.n, p.r);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
             set(it->second);
             return NMF_OK;
         }
+        // the planner's choice first; another height must be 5 % faster to replace it
+        int order[3] = {current, 0, 0}, k = 1;
+        for (int ba : cands)
+            if (ba != current) order[k++] = ba;
         int best = -1;
         float best_ms = 0.f;
-        for (int ba : cands) {
+        for (int ba : order) {
             if (ceil_div(rows, ba) > active_clusters(h, p.br, ba, p.r)[0]) continue;
             set(ba);
             int rc = plan_half_sweeps(h, p);
             if (rc) return rc;
             const float ms = time_half_sweep(h, launch_of());
             if (ms < 0.f) continue;
-            // a smaller tile must win by 3 % (it writes more Gram slabs)
-            if (best < 0 || ms < 0.97f * best_ms) {
+            if (best < 0 || ms < 0.95f * best_ms) {
                 best = ba;
                 best_ms = ms;
             }
         }
-        if (best < 0) best = 64;
+        if (best < 0) best = current;
         set(best);
         g_tune[key] = best;
+        if (std::getenv("NMF_DEBUG_PLAN")) std::fprintf(stderr, "nmf tune: %s -> %d rows\n", key.c_str(), best);
         return NMF_OK;
     };
-    int rc = pick('W', p.n,
+    int rc = pick('W', p.n, p.wtile,
                   [&](int ba) {
                       p.wtile = ba;
                       p.gb_count = (int)ceil_div(p.n, ba);
@@ -640,7 +645,7 @@ int tune_plan(nmf_ctx* h, Plan& p) {
                   [&]() { return p.lv[0].hsW; });
     if (rc) return rc;
     for (int l = 0; l < p.L; ++l) {
-        rc = pick('V', p.lv[l].m,
+        rc = pick('V', p.lv[l].m, p.lv[l].vtile,
                   [&](int ba) {
                       p.lv[l].vtile = ba;
                       p.lv[l].gd_count = (int)ceil_div(p.lv[l].m, ba);
