@@ -86,6 +86,20 @@ def _schedule_py(L, K):
     return counts
 
 
+def workload_config(args, world=1):
+    """The `config` object of the bench line (both arms)."""
+    from paper_1009_0881_gb300 import synth
+
+    gh, gw, n, r, _ = synth.WORKLOADS[args.workload]
+    sched = _schedule_py(args.levels, args.iters)
+    return {"workload": f"{args.workload}: {gh}x{gw} grid, m={gh * gw}, n={n}, r={r}; {args.algo} V-cycle "
+                        f"L={args.levels} K={args.iters} ({sum(sched)} sweeps) + final error",
+            "algo": args.algo, "levels": args.levels, "iters": args.iters,
+            "sweeps_per_step": sum(sched), "sweeps_per_level": sched,
+            "l2": "inputs (3.5 MB) fit in L2: a 258 MB buffer is written between timed steps",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_oracle_sample(args, K=None, levels=None):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -107,13 +121,14 @@ def reference_arm(args):
     sweeps = sum(s["sweeps"] for s in samples)
     secs = sum(s["seconds"] for s in samples)
     value = sweeps / secs
-    desc = (f"FP64 numpy oracle, single thread, {args.workload} {args.algo} V-cycle L={args.levels} with K=40 "
-            f"({samples[0]['sweeps']} sweeps) per step instead of K={args.iters}")
+    desc = (f"FP64 numpy oracle, single thread; each step a bounded sample of the workload: {args.workload} "
+            f"{args.algo} V-cycle L={args.levels} with K=40 ({samples[0]['sweeps']} sweeps) instead of "
+            f"K={args.iters}, throughput in sweeps/s")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "algo": args.algo, "levels": args.levels, "iters": 40},
+        "config": workload_config(args, 1),
         "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -293,12 +308,7 @@ def main_ours(args):
             "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator, CBCL-shaped 19x19 images)",
-            "config": {"workload": f"{args.workload}: 19x19 grid, m={m}, n={n}, r={r}; {args.algo} V-cycle "
-                                   f"L={args.levels} K={args.iters} ({sweeps_per_step} sweeps) + final error",
-                       "algo": args.algo, "levels": args.levels, "iters": args.iters,
-                       "sweeps_per_step": sweeps_per_step, "sweeps_per_level": sched,
-                       "l2": "inputs (3.5 MB) fit in L2: a 258 MB buffer is written between timed steps",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(args, world),
             "e2e": {"value": world * sweeps_per_step / (e2e_ms / 1e3), "unit": "sweeps/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
