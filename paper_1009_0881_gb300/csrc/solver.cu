@@ -145,6 +145,7 @@ struct Plan {
     float* PC = nullptr;  // reduced C^T = M^T V rows (ANLS)
     int gb_count = 0;
     int wtile = 64;       // rows of Wt per W-step tile (the same on every level: the slabs are shared)
+    int max_ctas = 0;     // CTAs a half-sweep may use (the SM count, or a share of it in a batch)
     int64_t slab = 0;     // floats per Gram slab (r x rp)
     int* err_flag = nullptr;
     double* err_part = nullptr;
@@ -447,15 +448,15 @@ int choose_cluster(int tiles, int ba, const int* active, int max_ctas) {
 // least 1.25x as many CTAs to win, since its product loop does fewer FMAs per
 // shared-memory load and it writes more Gram slabs.  Returns the height;
 // *cs_out the cluster size.
-int choose_tile(nmf_ctx* h, int br, int r, int64_t Na, int* cs_out) {
+int choose_tile(nmf_ctx* h, int br, int r, int64_t Na, int max_ctas, int* cs_out) {
     int best = 64, best_cs = 1;
     int64_t best_score = -1;
     for (int ba : {64, 32, 16}) {
         const int* act = active_clusters(h, br, ba, r);
         const int64_t tiles = ceil_div(Na, ba);
         if (tiles > act[0]) continue;
-        const int cs = choose_cluster((int)tiles, ba, act, h->num_sms);
-        const int64_t score = std::min<int64_t>(tiles * cs, h->num_sms);
+        const int cs = choose_cluster((int)tiles, ba, act, max_ctas);
+        const int64_t score = std::min<int64_t>(tiles * cs, max_ctas);
         if (best_score < 0 || 4 * score >= 5 * best_score) {
             if (best_score >= 0 && score == best_score) continue;
             best = ba;
@@ -480,7 +481,7 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
         a.tiles = v.gd_count;
         a.p.Na = (int)v.m;
         a.p.K = p.n;
-        a.p.cs = choose_cluster(a.tiles, a.ba, active_clusters(h, p.br, a.ba, p.r), h->num_sms);
+        a.p.cs = choose_cluster(a.tiles, a.ba, active_clusters(h, p.br, a.ba, p.r), p.max_ctas);
         a.p.kchunk = (int)round_up(ceil_div(p.n, a.p.cs), ks);
         a.p.r = p.r;
         a.p.rp = p.rp;
@@ -503,7 +504,7 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
         b.tiles = p.gb_count;
         b.p.Na = (int)p.n;
         b.p.K = v.m;
-        b.p.cs = choose_cluster(b.tiles, b.ba, active_w, h->num_sms);
+        b.p.cs = choose_cluster(b.tiles, b.ba, active_w, p.max_ctas);
         b.p.kchunk = (int)round_up(ceil_div(v.m, b.p.cs), ks);
         b.p.r = p.r;
         b.p.rp = p.rp;
@@ -534,7 +535,8 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p) {
     return NMF_OK;
 }
 
-void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap);
+void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap,
+               int max_ctas = 0);
 
 // ---------------------------------------------------------------------------
 // Autotuner of the half-sweep tile heights.  The planner's choice (choose_tile)
@@ -563,7 +565,7 @@ bool tune_enabled() {
 
 // Tiles already tuned for this shape (plan_dims applies them).
 void apply_tuned(nmf_ctx* h, Plan& p) {
-    if (p.bf16 || !tune_enabled()) return;
+    if (p.bf16 || !tune_enabled() || p.max_ctas < h->num_sms) return;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key('W', h->device, p.n, p.lv[0].m, p.r));
     if (it != g_tune.end()) p.wtile = it->second;
@@ -603,7 +605,7 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p);
 
 // Time the candidates of every untuned half-sweep of p and record the fastest.
 int tune_plan(nmf_ctx* h, Plan& p) {
-    if (p.bf16 || !tune_enabled()) return NMF_OK;
+    if (p.bf16 || !tune_enabled() || p.max_ctas < h->num_sms) return NMF_OK;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int cands[3] = {64, 32, 16};
     auto pick = [&](char which, int64_t rows, int current, auto set, auto launch_of) -> int {
@@ -700,7 +702,8 @@ int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, 
     return tune_plan(h, p);
 }
 
-void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap) {
+void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap,
+               int max_ctas) {
     p.m = m;
     p.n = n;
     p.r = r;
@@ -710,7 +713,8 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
     // W-step tile height chosen on the finest level (the W-step tiles and their Gram
     // slabs are shared by all levels); V-step tiles per level.  The BF16 form's row
     // update works on 64-row tiles.
-    p.wtile = p.bf16 ? 64 : choose_tile(h, p.br, r, n, nullptr);
+    p.max_ctas = max_ctas > 0 ? std::min(max_ctas, h->num_sms) : h->num_sms;
+    p.wtile = p.bf16 ? 64 : choose_tile(h, p.br, r, n, p.max_ctas, nullptr);
     p.L = L;
     p.ldm = round_up(n, 4);
     p.trace_cap = trace_cap;
@@ -724,7 +728,7 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
         ww = (ww + 1) / 2;
     }
     for (int l = 0; l < L; ++l)
-        p.lv[l].vtile = p.bf16 ? 64 : choose_tile(h, p.br, r, p.lv[l].m, nullptr);
+        p.lv[l].vtile = p.bf16 ? 64 : choose_tile(h, p.br, r, p.lv[l].m, p.max_ctas, nullptr);
     apply_tuned(h, p);
 }
 
