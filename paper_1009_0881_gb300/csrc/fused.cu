@@ -65,6 +65,20 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 __host__ __device__ inline int slab_f4(int r, int rp) { return r * rp / 4; }
 __host__ __device__ inline int slice_f4(int r, int rp, int cs) { return (slab_f4(r, rp) + cs - 1) / cs; }
 
+// Sum of one double per thread over the CTA, in a fixed order (warp butterflies,
+// then the warps in order); the result is valid in thread 0.  `red` holds NT/32 doubles.
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
 __host__ __device__ inline Smem smem_layout(int br, int BA, int r, int rp, int cs) {
     Smem s{};
     size_t o = 0;
@@ -328,6 +342,16 @@ __global__ void __launch_bounds__(NT, 1)
         __syncthreads();
         rowupd::update_rows_any<MODE>(p.F, p.Na, r, rp, R, (int64_t)a0 + row0, Fn, Ared, Dn, Gs, Ginv);
         __syncthreads();
+        if (p.obj_part) {
+            // objective identity, first term: <P_i, new F_i> over this CTA's rows (FP64)
+            double t = 0.0;
+            for (int e = tid; e < R * r; e += NT) {
+                const int rr = e / r, k = e - rr * r;
+                t += (double)Ared[rr * kMaxRank + k] * (double)Fn[rr * kMaxRank + k];
+            }
+            t = block_sum_d(t, reinterpret_cast<double*>(Part));
+            if (tid == 0) p.obj_part[2 * blockIdx.x] = t;
+        }
         // partial Gram of this CTA's new rows, 4 x 4 outputs per thread (rows past Na are zero)
         {
             float ga[4][4];
@@ -364,10 +388,20 @@ __global__ void __launch_bounds__(NT, 1)
         // Nothing reads another rank's shared memory after #3, so no closing barrier.
         float4* gout = reinterpret_cast<float4*>(p.Gout + (int64_t)tile * p.gout_stride);
         const int n4 = max(0, min(S4, F4 - crank * S4));
+        double t2 = 0.0;
         for (int j = tid; j < n4; j += NT) {
             float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int c = 0; c < cs; ++c) s = f4add(s, reinterpret_cast<const float4*>(Fg)[c * S4 + j]);
             gout[crank * S4 + j] = s;
+            if (p.obj_part) {
+                const float4 g4 = reinterpret_cast<const float4*>(Gs)[crank * S4 + j];
+                t2 += (double)s.x * g4.x + (double)s.y * g4.y + (double)s.z * g4.z + (double)s.w * g4.w;
+            }
+        }
+        if (p.obj_part) {
+            // second term: <G, slab slice>; G here is the Gram matrix this half-sweep used
+            t2 = block_sum_d(t2, reinterpret_cast<double*>(Part));
+            if (tid == 0) p.obj_part[2 * blockIdx.x + 1] = t2;
         }
     }
 }

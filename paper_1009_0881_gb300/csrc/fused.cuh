@@ -25,6 +25,8 @@ struct HalfSweepParams {
     float* Pout;       // STORE mode: reduced product rows, Na x rp
     int* err_flag;     // set to 1 if a bounded wait gave up
     const int* skip;   // optional: when *skip != 0 the launch does nothing (converged problem)
+    double* obj_part;  // optional (HALS / MU): per-CTA terms of the objective identity, 2 per CTA:
+                       // [2b] = <P rows, new F rows>, [2b+1] = <G, this CTA's slice of the new slab>
 };
 
 struct HalfSweepLaunch {

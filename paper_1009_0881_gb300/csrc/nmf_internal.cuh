@@ -109,6 +109,13 @@ cudaError_t check_nonneg_launch(const float* X, int64_t ld, int64_t rows, int64_
 // ---------------------------------------------------------------------------
 int64_t error_partials_needed(int64_t m, int64_t n);
 // Batched stopping rule: sets *flag once |f_prev - f_now| <= tol * f_now; counts sweeps run.
+// ||M||_F of a rows x cols matrix (FP64), through up to max_partials per-block sums.
+cudaError_t norm_launch(const float* M, int64_t ld, int64_t rows, int64_t cols, double* d_partials, int64_t max_partials,
+                        double* d_out, cudaStream_t st);
+// Objective after a sweep from the identity terms written by the W-step half-sweep
+// (HalfSweepParams::obj_part, nblocks CTAs) and ||M||_F.
+cudaError_t identity_objective_launch(const double* part, int nblocks, const double* mnorm, double* f_out,
+                                      const int* skip, cudaStream_t st);
 cudaError_t converge_check_launch(const double* f_now, double* state, int* flag, double tol, long long* count,
                                   cudaStream_t st);
 cudaError_t error_launch(const float* M, int64_t ldm, const float* V, const float* Wt, int64_t rp,

@@ -150,6 +150,8 @@ struct Plan {
     int* err_flag = nullptr;
     double* err_part = nullptr;
     double* Gd = nullptr;  // ANLS: FP64 Gram matrix (r x r)
+    double* obj_part = nullptr;  // objective identity terms of a W-step (2 per CTA)
+    double* mnorm = nullptr;     // ||M||_F of the finest level
     double* err_out = nullptr;
     double* d_trace = nullptr;
     int* d_status = nullptr;
@@ -321,6 +323,8 @@ void layout(Plan& p, Bump& b, int num_sms) {
     p.err_flag = b.take<int>(1);
     p.err_part = b.take<double>((size_t)error_partials_needed(p.lv[0].m, n));
     p.Gd = b.take<double>((size_t)p.r * p.r);
+    p.obj_part = b.take<double>((size_t)2 * std::max<int64_t>(ceil_div(n, 16), num_sms));
+    p.mnorm = b.take<double>(1);
     p.err_out = b.take<double>(1);
     p.d_trace = b.take<double>((size_t)(p.trace_cap > 0 ? p.trace_cap : 1));
     p.d_status = b.take<int>(1);
@@ -738,7 +742,7 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
 // Wt and their B slabs).  HALS and MU update inside the fused kernel; ANLS
 // stores the reduced products and runs the active-set solver on them.
 cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64_t* launches,
-                          const int* skip = nullptr) {
+                          const int* skip = nullptr, double* obj_part = nullptr) {
     const Level& v = p.lv[l];
     const int mode = algo == NMF_HALS ? kModeHals : (algo == NMF_MU ? kModeMu : kModeStore);
     HalfSweepLaunch a = v.hsV;
@@ -770,6 +774,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
     HalfSweepLaunch b = v.hsW;
     b.mode = mode;
     b.p.skip = skip;
+    b.p.obj_part = mode == kModeStore ? nullptr : obj_part;
     e = half_sweep_launch(b, h->stream);
     if (e != cudaSuccess) return e;
     ++*launches;
@@ -906,8 +911,14 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
     for (int i = 0; i < (int)ops.size(); ++i)
         if (ops[i].kind == OP_SWEEPS && ops[i].level == 0) last_fine = i;
     const bool stop_rule = rel_tol > 0.0 && algo != NMF_ANLS && last_fine >= 0;
+    // FP32 form: the stopping rule reads the objective from the identity terms of the
+    // W-step (no extra pass over M); it needs ||M||_F of the finest level once
+    const bool identity = stop_rule && !p.bf16;
     // B = W W^T slabs of the initial W, consumed by the first V-step
     cudaError_t e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream);
+    if (e == cudaSuccess && identity)
+        e = norm_launch(p.lv[0].M, p.ldm, p.lv[0].m, p.n, p.err_part, error_partials_needed(p.lv[0].m, p.n), p.mnorm,
+                        h->stream);
     if (e != cudaSuccess) return e;
     for (int oi = 0; oi < (int)ops.size(); ++oi) {
         const Op& op = ops[oi];
@@ -924,12 +935,16 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
                 if (stop_after > 0 && done >= stop_after) break;
                 const int* skip = watched ? p.conv_flag : nullptr;
                 e = p.bf16 ? enqueue_sweep_bf16(h, p, op.level, algo, skip)
-                           : enqueue_sweep(h, p, op.level, algo, &launches, skip);
+                           : enqueue_sweep(h, p, op.level, algo, &launches, skip, watched ? p.obj_part : nullptr);
                 if (e != cudaSuccess) return e;
                 ++done;
                 if (watched) {
-                    e = error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, f.m, p.n, p.r, p.err_part, p.conv_state + 1,
-                                     h->stream);
+                    if (identity)
+                        e = identity_objective_launch(p.obj_part, f.hsW.tiles * f.hsW.p.cs, p.mnorm, p.conv_state + 1,
+                                                      p.conv_flag, h->stream);
+                    else
+                        e = error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, f.m, p.n, p.r, p.err_part, p.conv_state + 1,
+                                         h->stream);
                     if (e == cudaSuccess)
                         e = converge_check_launch(p.conv_state + 1, p.conv_state, p.conv_flag, rel_tol, p.conv_count,
                                                   h->stream);

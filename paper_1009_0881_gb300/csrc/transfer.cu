@@ -1,3 +1,4 @@
+#include <algorithm>
 // Grid transfer operators of Section 4.2, layout helpers, input checks and the
 // Frobenius error.
 //
@@ -332,6 +333,57 @@ __global__ void converge_check_kernel(const double* __restrict__ f_now, double* 
     state[0] = cur;
 }
 }  // namespace
+
+namespace {
+// Per-block FP64 sums of squares of a row-major matrix (rows x cols, leading dimension ld).
+__global__ void sumsq_kernel(const float* __restrict__ M, int64_t ld, int64_t rows, int64_t cols,
+                             double* __restrict__ partials) {
+    __shared__ double red[256];
+    double s = 0.0;
+    const int64_t total = rows * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / cols, j = t - i * cols;
+        const double v = M[i * ld + j];
+        s += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+// f = sqrt(max(0, ||M||^2 - 2 sum_b part[2b] + sum_b part[2b+1])): the objective
+// after a sweep from the identity ||M - VW||^2 = ||M||^2 - 2 <V^T M, W> + <V^T V, W W^T>,
+// blocks summed in index order.  Does nothing once the problem is flagged converged.
+__global__ void identity_objective_kernel(const double* __restrict__ part, int nblocks, const double* __restrict__ mnorm,
+                                          double* __restrict__ f_out, const int* skip) {
+    if (skip && *skip) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        s1 += part[2 * b];
+        s2 += part[2 * b + 1];
+    }
+    const double m = *mnorm;
+    *f_out = sqrt(fmax(0.0, m * m - 2.0 * s1 + s2));
+}
+}  // namespace
+
+cudaError_t norm_launch(const float* M, int64_t ld, int64_t rows, int64_t cols, double* d_partials, int64_t max_partials,
+                        double* d_out, cudaStream_t st) {
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(max_partials, 256));
+    sumsq_kernel<<<(unsigned)blocks, 256, 0, st>>>(M, ld, rows, cols, d_partials);
+    sum_partials_kernel<<<1, 256, 0, st>>>(d_partials, blocks, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t identity_objective_launch(const double* part, int nblocks, const double* mnorm, double* f_out,
+                                      const int* skip, cudaStream_t st) {
+    identity_objective_kernel<<<1, 1, 0, st>>>(part, nblocks, mnorm, f_out, skip);
+    return cudaGetLastError();
+}
 
 cudaError_t converge_check_launch(const double* f_now, double* state, int* flag, double tol, long long* count,
                                   cudaStream_t st) {
