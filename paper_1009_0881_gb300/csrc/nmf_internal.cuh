@@ -120,6 +120,6 @@ cudaError_t converge_check_launch(const double* f_now, double* state, int* flag,
                                   cudaStream_t st);
 cudaError_t error_launch(const float* M, int64_t ldm, const float* V, const float* Wt, int64_t rp,
                          int64_t m, int64_t n, int r, double* d_partials, double* d_out,
-                         cudaStream_t st);
+                         cudaStream_t st, const int* skip = nullptr);
 
 }  // namespace nmfk

@@ -944,7 +944,7 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
                                                       p.conv_flag, h->stream);
                     else
                         e = error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, f.m, p.n, p.r, p.err_part, p.conv_state + 1,
-                                         h->stream);
+                                         h->stream, p.conv_flag);
                     if (e == cudaSuccess)
                         e = converge_check_launch(p.conv_state + 1, p.conv_state, p.conv_flag, rel_tol, p.conv_count,
                                                   h->stream);

@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(256) error_tile_kernel(const float* __restrict
                                                          const float* __restrict__ V,
                                                          const float* __restrict__ Wt, int64_t rp,
                                                          int64_t m, int64_t n, int r,
-                                                         double* __restrict__ partials) {
+                                                         double* __restrict__ partials, const int* skip) {
+    if (skip && *(volatile const int*)skip) return;
     __shared__ float Vs[kMaxRank][kErrTile + 4];
     __shared__ float Ws[kMaxRank][kErrTile + 1];
     const int64_t ntj = ceil_div(n, kErrTile);
@@ -215,7 +216,9 @@ __global__ void __launch_bounds__(256) error_tile_kernel(const float* __restrict
     if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
 }
 
-__global__ void sum_partials_kernel(const double* __restrict__ partials, int64_t count, double* out) {
+__global__ void sum_partials_kernel(const double* __restrict__ partials, int64_t count, double* out,
+                                    const int* skip = nullptr) {
+    if (skip && *(volatile const int*)skip) return;
     __shared__ double red[256];
     double s = 0.0;
     for (int64_t t = threadIdx.x; t < count; t += blockDim.x) s += partials[t];
@@ -313,10 +316,10 @@ int64_t error_partials_needed(int64_t m, int64_t n) {
 }
 
 cudaError_t error_launch(const float* M, int64_t ldm, const float* V, const float* Wt, int64_t rp, int64_t m,
-                         int64_t n, int r, double* d_partials, double* d_out, cudaStream_t st) {
+                         int64_t n, int r, double* d_partials, double* d_out, cudaStream_t st, const int* skip) {
     const int64_t tiles = error_partials_needed(m, n);
-    error_tile_kernel<<<(unsigned)tiles, 256, 0, st>>>(M, ldm, V, Wt, rp, m, n, r, d_partials);
-    sum_partials_kernel<<<1, 256, 0, st>>>(d_partials, tiles, d_out);
+    error_tile_kernel<<<(unsigned)tiles, 256, 0, st>>>(M, ldm, V, Wt, rp, m, n, r, d_partials, skip);
+    sum_partials_kernel<<<1, 256, 0, st>>>(d_partials, tiles, d_out, skip);
     return cudaGetLastError();
 }
 
