@@ -258,6 +258,18 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                       const float* V, const float* W, int reps, float* ms_out);
 
 /*
+ * nmf_profile_coarse - timing of the persistent coarse-level kernel, which a
+ * solve uses for the HALS / MU sweeps (Algorithms 2 and 3) on coarse levels
+ * (Section 4.2) of the FP32 form whose V has at most 32 rows: one untimed run,
+ * then one run of `sweeps` sweeps between CUDA events on the handle's stream;
+ * *ms_out receives the mean time of one sweep.  M (m x n), V, W as in
+ * nmf_sweep, read only.  NMF_EINVAL if the kernel does not apply to this
+ * shape, algorithm or precision (or NMF_COARSE=0 disables it).
+ */
+int nmf_profile_coarse(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo,
+                       const float* V, const float* W, int sweeps, float* ms_out);
+
+/*
  * nmf_error_noalloc - ||M - VW||_F, the same value as nmf_error, computed
  * without allocating any device memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc, such as a

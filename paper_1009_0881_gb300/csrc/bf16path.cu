@@ -114,25 +114,29 @@ __device__ __forceinline__ void hals_rows_quad(int r, int rp, float* Fn, const f
         g[4 * v + 2] = gv.z;
         g[4 * v + 3] = gv.w;
     }
+    // k = 16 q0 + i0: the block loop stays rolled (compact code), the steps inside
+    // are unrolled so that the owner's entry i0 is a register
+    for (int q0 = 0; q0 < 4 && 16 * q0 < r; ++q0) {
 #pragma unroll
-    for (int k = 0; k < kMaxRank; ++k) {
-        if (k < r) {
-            const int q0 = k >> 4, i0 = k & 15;
-            float dl = 0.f;
-            if (qd == q0) {
-                const float nv = fmaxf(0.f, fmaf(g[i0], Ginv[k], f[i0]));
-                dl = nv - f[i0];
-                f[i0] = nv;
-            }
-            const float d = __shfl_sync(0xffffffffu, dl, gbase + q0);
-            const float4* gk = reinterpret_cast<const float4*>(G64 + k * kMaxRank + 16 * qd);
+        for (int i0 = 0; i0 < 16; ++i0) {
+            const int k = 16 * q0 + i0;
+            if (k < r) {
+                float dl = 0.f;
+                if (qd == q0) {
+                    const float nv = fmaxf(0.f, fmaf(g[i0], Ginv[k], f[i0]));
+                    dl = nv - f[i0];
+                    f[i0] = nv;
+                }
+                const float d = __shfl_sync(0xffffffffu, dl, gbase + q0);
+                const float4* gk = reinterpret_cast<const float4*>(G64 + k * kMaxRank + 16 * qd);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const float4 gv = gk[v];
-                g[4 * v] = fmaf(-d, gv.x, g[4 * v]);
-                g[4 * v + 1] = fmaf(-d, gv.y, g[4 * v + 1]);
-                g[4 * v + 2] = fmaf(-d, gv.z, g[4 * v + 2]);
-                g[4 * v + 3] = fmaf(-d, gv.w, g[4 * v + 3]);
+                for (int v = 0; v < 4; ++v) {
+                    const float4 gv = gk[v];
+                    g[4 * v] = fmaf(-d, gv.x, g[4 * v]);
+                    g[4 * v + 1] = fmaf(-d, gv.y, g[4 * v + 1]);
+                    g[4 * v + 2] = fmaf(-d, gv.z, g[4 * v + 2]);
+                    g[4 * v + 3] = fmaf(-d, gv.w, g[4 * v + 3]);
+                }
             }
         }
     }

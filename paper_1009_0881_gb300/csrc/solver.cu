@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "coarse.cuh"
 #include "fused.cuh"
 #include "nmf_internal.cuh"
 #include "tc_gemm.cuh"
@@ -120,6 +121,10 @@ struct Level {
     HalfSweepLaunch hsV{}, hsW{};     // fused half-sweeps of the solve
     int gd_count = 0;                 // D partial slabs written by the V-step (one per tile of V)
     int vtile = 64;                   // rows of V per V-step tile
+    // coarse levels of the FP32 form: HALS / MU runs in one persistent launch (coarse.cu)
+    bool crun = false;
+    int ccpc = 0, cnchunk = 0, cgrid = 0;
+    size_t csmem = 0;
     // BF16 precision form: operand copies, descriptors and tcgen05 products
     __nv_bfloat16* Mb = nullptr;   // m x ldmb
     __nv_bfloat16* Mtb = nullptr;  // n x ldmtb
@@ -147,6 +152,10 @@ struct Plan {
     int wtile = 64;       // rows of Wt per W-step tile (the same on every level: the slabs are shared)
     int max_ctas = 0;     // CTAs a half-sweep may use (the SM count, or a share of it in a batch)
     int64_t slab = 0;     // floats per Gram slab (r x rp)
+    float* cpart = nullptr;   // coarse runs: per-chunk partial products
+    float* cred = nullptr;    // coarse runs: reduced products of a V-step
+    unsigned* cbar = nullptr; // coarse runs: grid-barrier counter
+    bool coarse_l0 = false;   // let level 0 use the coarse-run kernel too (nmf_profile_coarse)
     int* err_flag = nullptr;
     double* err_part = nullptr;
     double* Gd = nullptr;  // ANLS: FP64 Gram matrix (r x r)
@@ -249,6 +258,12 @@ int pick_br(int rp) {
 
 constexpr int kMaxSplits = 32;
 
+// NMF_COARSE=0 runs coarse levels with the half-sweep kernels as well.
+bool coarse_enabled() {
+    const char* e = std::getenv("NMF_COARSE");
+    return !(e && e[0] == '0');
+}
+
 // Lay out (or size, when b.dry) the workspace of a solve.
 void layout(Plan& p, Bump& b, int num_sms) {
     const int64_t n = p.n, rp = p.rp;
@@ -318,6 +333,22 @@ void layout(Plan& p, Bump& b, int num_sms) {
     }
     p.GB = b.take<float>((size_t)(ceil_div(n, min_tile) * p.slab));
     p.GD = b.take<float>((size_t)(max_gd * p.slab));
+    // coarse levels that run their sweeps in one persistent launch (FP32 form)
+    int64_t max_cpart = 0, max_cred = 0;
+    for (int l = p.coarse_l0 ? 0 : 1; l < p.L; ++l) {
+        Level& v = p.lv[l];
+        v.crun = !p.bf16 && coarse_enabled() &&
+                 coarse_fits(v.m, n, p.r, num_sms, &v.csmem, &v.ccpc, &v.cnchunk, &v.cgrid);
+        if (v.crun) {
+            max_cpart = std::max<int64_t>(max_cpart, v.cnchunk * coarse_slot_floats(v.m, p.r, p.rp));
+            max_cred = std::max<int64_t>(max_cred, (v.m + p.r) * rp);
+        }
+    }
+    if (max_cpart > 0) {
+        p.cpart = b.take<float>((size_t)max_cpart);
+        p.cred = b.take<float>((size_t)max_cred);
+        p.cbar = b.take<unsigned>(1);
+    }
     p.PA = b.take<float>((size_t)(p.lv[0].m * rp));
     p.PC = b.take<float>((size_t)(n * rp));
     p.err_flag = b.take<int>(1);
@@ -742,12 +773,13 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
 // Wt and their B slabs).  HALS and MU update inside the fused kernel; ANLS
 // stores the reduced products and runs the active-set solver on them.
 cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64_t* launches,
-                          const int* skip = nullptr, double* obj_part = nullptr) {
+                          const int* skip = nullptr, double* obj_part = nullptr, bool gb_single = false) {
     const Level& v = p.lv[l];
     const int mode = algo == NMF_HALS ? kModeHals : (algo == NMF_MU ? kModeMu : kModeStore);
     HalfSweepLaunch a = v.hsV;
     a.mode = mode;
     a.p.skip = skip;
+    if (gb_single) a.p.gin_count = 1;  // B whole in slab 0 (written by a coarse run)
     cudaError_t e = half_sweep_launch(a, h->stream);
     if (e != cudaSuccess) return e;
     ++*launches;
@@ -799,6 +831,31 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         *launches += 3;
     }
     return cudaSuccess;
+}
+
+// All `count` sweeps of a run at coarse level l in one persistent launch; leaves
+// B = W W^T of the final W in slab 0 of GB.
+cudaError_t enqueue_coarse_run(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64_t count) {
+    const Level& v = p.lv[l];
+    CoarseParams q{};
+    q.M = v.M;
+    q.ldm = p.ldm;
+    q.V = v.V;
+    q.Wt = p.Wt;
+    q.m = (int)v.m;
+    q.n = (int)p.n;
+    q.r = p.r;
+    q.rp = p.rp;
+    q.sweeps = (int)count;
+    q.nchunk = v.cnchunk;
+    q.cpc = v.ccpc;
+    q.part = p.cpart;
+    q.part_stride = coarse_slot_floats(v.m, p.r, p.rp);
+    q.red = p.cred;
+    q.Bout = p.GB;
+    q.bar = p.cbar;
+    q.err_flag = p.err_flag;
+    return coarse_run_launch(q, algo == NMF_HALS ? 0 : 1, v.cgrid, v.csmem, h->stream);
 }
 
 // Restrictions of M for every level (computed once per solve, footnote of
@@ -920,6 +977,7 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
         e = norm_launch(p.lv[0].M, p.ldm, p.lv[0].m, p.n, p.err_part, error_partials_needed(p.lv[0].m, p.n), p.mnorm,
                         h->stream);
     if (e != cudaSuccess) return e;
+    bool gb_single = false;  // GB holds the whole of B in slab 0 (after a coarse run)
     for (int oi = 0; oi < (int)ops.size(); ++oi) {
         const Op& op = ops[oi];
         const Level& f = p.lv[op.level];
@@ -930,12 +988,24 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
         } else if (op.kind == OP_PROLONG_V) {
             const Level& c = p.lv[op.level + 1];
             e = prolong_launch(c.V, p.rp, f.h, f.w, p.rp, f.V, p.rp, h->stream);
+        } else if (f.crun && algo != NMF_ANLS && op.level > 0 && !watched) {
+            int64_t cnt = op.count;
+            if (stop_after > 0) cnt = std::min<int64_t>(cnt, std::max<int64_t>(0, stop_after - done));
+            if (cnt > 0) {
+                e = enqueue_coarse_run(h, p, op.level, algo, cnt);
+                if (e != cudaSuccess) return e;
+                ++launches;
+                done += cnt;
+                gb_single = true;
+            }
         } else {
             for (int64_t s = 0; s < op.count; ++s) {
                 if (stop_after > 0 && done >= stop_after) break;
                 const int* skip = watched ? p.conv_flag : nullptr;
                 e = p.bf16 ? enqueue_sweep_bf16(h, p, op.level, algo, skip)
-                           : enqueue_sweep(h, p, op.level, algo, &launches, skip, watched ? p.obj_part : nullptr);
+                           : enqueue_sweep(h, p, op.level, algo, &launches, skip, watched ? p.obj_part : nullptr,
+                                           gb_single);
+                gb_single = false;
                 if (e != cudaSuccess) return e;
                 ++done;
                 if (watched) {
@@ -1306,7 +1376,7 @@ int nmf_create(nmf_handle* out, int device, size_t hbm_budget_bytes, nmf_precisi
     }
     h->stream = h->own_stream;
     if (init_kernel_attributes() != cudaSuccess || tma_init() != cudaSuccess || half_sweep_init() != cudaSuccess ||
-        tc_gemm_init() != cudaSuccess || rows_update_init() != cudaSuccess) {
+        tc_gemm_init() != cudaSuccess || rows_update_init() != cudaSuccess || coarse_init() != cudaSuccess) {
         cudaGetLastError();
         nmf_destroy(h);
         return NMF_ECUDA;
@@ -1633,6 +1703,52 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return out_rc;
+}
+
+int nmf_profile_coarse(nmf_handle h, const float* M, int64_t m, int64_t n, int r, nmf_algo algo, const float* V,
+                       const float* W, int sweeps, float* ms_out) {
+    if (!h) return NMF_EINVAL;
+    int rc = check_dims(h, m, n, r);
+    if (rc) return rc;
+    if (!M || !V || !W || !ms_out || sweeps < 1) return fail(h, NMF_EINVAL, "bad profile arguments");
+    if (algo != NMF_HALS && algo != NMF_MU) return fail(h, NMF_EINVAL, "the coarse-run kernel does HALS and MU only");
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+    Plan p;
+    plan_dims(h, p, m, n, (int)m, 1, r, 1, 0);
+    p.coarse_l0 = true;
+    Bump dry;
+    layout(p, dry, h->num_sms);
+    if (!p.lv[0].crun) return fail(h, NMF_EINVAL, "the coarse-run kernel does not apply to this shape or precision");
+    rc = ensure_workspace(h, dry.off);
+    if (rc) return rc;
+    Bump real;
+    real.dry = false;
+    real.base = h->ws;
+    real.cap = h->ws_cap;
+    layout(p, real, h->num_sms);
+    rc = stage_problem(h, p, M, V, W);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    cudaError_t e = enqueue_coarse_run(h, p, 0, algo, sweeps);  // untimed
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    if (e == cudaSuccess) e = enqueue_coarse_run(h, p, 0, algo, sweeps);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(h, NMF_ECUDA, "coarse profile failed: %s", cudaGetErrorString(e));
+    h->launches = 2;
+    int flag = 0;
+    CK(cudaMemcpy(&flag, p.err_flag, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) return fail(h, NMF_ETIMEOUT, "a grid barrier of the coarse-run kernel gave up waiting");
+    *ms_out = ms / sweeps;
+    return NMF_OK;
 }
 
 }  // extern "C"

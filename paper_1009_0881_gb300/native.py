@@ -43,6 +43,7 @@ SIGNATURES = [
     ("nmf_set_stream", _I, [_P, _P]),
     ("nmf_last_launch_count", _I64, [_P]),
     ("nmf_profile_sweep", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
+    ("nmf_profile_coarse", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
     ("nmf_error_noalloc", _I, [_P, _P, _P, _I64, _I64, _I, _P, ctypes.POINTER(ctypes.c_double)]),
     ("nmf_solve_batch", _I, [_P, _P, _I]),
     ("nmf_workspace_bytes", _I64, [_P, _P, _I]),
@@ -269,6 +270,20 @@ class Handle:
         a = ALGOS[algo] if isinstance(algo, str) else int(algo)
         self._rc(self.lib.nmf_profile_sweep(self.h, _ptr(M), m, n, V.shape[1], a, _ptr(V), _ptr(W), reps, out))
         return list(out)
+
+    def profile_coarse(self, M, V, W, algo="hals", sweeps: int = 100) -> float | None:
+        """nmf_profile_coarse: mean ms per sweep of the persistent coarse-level kernel,
+        or None when the kernel does not apply to this shape (NMF_EINVAL)."""
+        _check_f32(M, V, W)
+        m, n = M.shape
+        out = ctypes.c_float(0.0)
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        rc = self.lib.nmf_profile_coarse(self.h, _ptr(M), m, n, V.shape[1], a, _ptr(V), _ptr(W), sweeps,
+                                         ctypes.byref(out))
+        if rc == -1:  # NMF_EINVAL
+            return None
+        self._rc(rc)
+        return float(out.value)
 
 
 def fill_problem(q: Problem, d: dict) -> Problem:

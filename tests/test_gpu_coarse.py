@@ -1,0 +1,98 @@
+"""The persistent coarse-level kernel (FP32 HALS and MU sweeps on coarse levels
+whose V has at most 32 rows, all sweeps of a run in one launch).
+
+Its cycles are checked against the FP64 oracle and against the same cycles run
+with the half-sweep kernels only (NMF_COARSE=0), which differ from it only in
+the order of floating-point sums; a stop_after that ends inside a coarse run is
+checked the same way; and its timing entry point reports a time for eligible
+shapes and NMF_EINVAL (None) for others."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import nmf_oracle as o
+from paper_1009_0881_gb300 import native, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1009_0881_gb300 import build
+    build.build()
+    return True
+
+
+def _solve(problem, case, coarse: bool, **kw):
+    gh, gw, n, r, L, K, algo = case
+    old = os.environ.get("NMF_COARSE")
+    os.environ["NMF_COARSE"] = "1" if coarse else "0"
+    try:
+        with native.Handle(0) as h:  # a fresh handle: plans and graphs are made under the setting
+            V, W = problem.V.copy(), problem.W.copy()
+            h.solve(problem.M, gh, gw, V, W, algo, levels=L, iters=K, **kw)
+    finally:
+        if old is None:
+            del os.environ["NMF_COARSE"]
+        else:
+            os.environ["NMF_COARSE"] = old
+    return V, W
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+CASES = [  # (grid_h, grid_w, n, r, levels, K, algo); the coarsest level has <= 32 pixels
+    (19, 19, 300, 12, 3, 8, "hals"),   # 19x19 -> 10x10 -> 5x5 (25 rows)
+    (16, 16, 400, 49, 3, 8, "mu"),     # 16x16 -> 8x8 -> 4x4 (16 rows)
+    (12, 9, 2429, 49, 2, 8, "hals"),   # 108 -> 30 rows, 152 column chunks
+    (8, 8, 5000, 64, 2, 6, "hals"),    # 64 -> 16 rows, more chunks than SMs, rank 64
+    (7, 9, 65, 17, 3, 4, "hals"),      # ragged: 5 chunks, the last one partial
+    (3, 3, 20, 1, 2, 4, "mu"),         # rank 1, a 2 x 2 coarse grid, one chunk
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}_n{c[2]}_r{c[3]}_L{c[4]}_{c[6]}" for c in CASES])
+def test_coarse_cycle_matches_oracle_and_half_sweep_path(built, case):
+    gh, gw, n, r, L, K, algo = case
+    p = synth.make_problem(gh, gw, n, r, sigma=1.0, data_seed=5)
+    V, W = _solve(p, case, coarse=True)
+    assert np.isfinite(V).all() and np.isfinite(W).all()
+    assert (V >= 0).all() and (W >= 0).all()
+    Vo, Wo = o.solve(p.M, gh, gw, p.V, p.W, algo, levels=L, K=K)
+    f, fo = o.objective(p.M, V, W), o.objective(p.M, Vo, Wo)
+    mnorm = float(np.linalg.norm(p.M.astype(np.float64)))
+    assert abs(f - fo) <= max(1e-4 * fo, 1e-6 * mnorm), (f, fo)
+    # the half-sweep kernels on the same cycle: the same arithmetic up to summation order
+    V0, W0 = _solve(p, case, coarse=False)
+    assert rel(V @ W, V0 @ W0) <= 1e-4
+    assert abs(f - o.objective(p.M, V0, W0)) <= max(1e-5 * f, 1e-6 * mnorm)
+
+
+def test_stop_after_inside_a_coarse_run(built):
+    # V-cycle on 16x16, L = 3, K = 40: 10 fine, 10 on 8x8, 40 on 4x4 (coarse run), 20, 20;
+    # stopping after 45 sweeps ends 25 sweeps into the coarse run
+    case = (16, 16, 1000, 10, 3, 40, "hals")
+    p = synth.make_problem(16, 16, 1000, 10, data_seed=3)
+    V1, W1 = _solve(p, case, coarse=True, stop_after=45)
+    V0, W0 = _solve(p, case, coarse=False, stop_after=45)
+    assert rel(V1 @ W1, V0 @ W0) <= 1e-4
+    # and it really stopped there: the full cycle goes further
+    V2, W2 = _solve(p, case, coarse=True)
+    assert o.objective(p.M, V2, W2) < o.objective(p.M, V1, W1)
+
+
+def test_profile_coarse(built):
+    with native.Handle(0) as h:
+        p = synth.make_problem(5, 5, 2429, 49, data_seed=1)
+        ms = h.profile_coarse(p.M, p.V, p.W, "hals", sweeps=20)
+        assert ms is not None and 0.0 < ms < 1.0  # milliseconds per sweep
+        q = synth.make_problem(10, 10, 500, 12, data_seed=1)  # 100 rows: not a coarse-run shape
+        assert h.profile_coarse(q.M, q.V, q.W, "hals", sweeps=5) is None
+        assert h.profile_coarse(p.M, p.V, p.W, "anls", sweeps=5) is None
