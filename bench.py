@@ -418,10 +418,10 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
 # valid while the kernel's sources hash to `src`; the captures and their commands are
 # summarised under profiles/.
 TRAFFIC = {
-    "half_sweep_kernel": {"bytes": 0.5 * (4.965888e6 + 4.228864e6), "src": "9e18b058e8e21ec8",
+    "half_sweep_kernel": {"bytes": 0.5 * (4.968704e6 + 4.231936e6), "src": "a15ed2a98ec25cc9",
                           "files": ("fused.cu", "fused.cuh", "rowupdate.cuh", "ptx.cuh", "nmf_internal.cuh"),
                           "scope": "mean of the finest-level V-step (64-row tiles) and W-step (32-row tiles) launches, 19x19 grid n=2429 r=49"},
-    "tc_gemm_kernel": {"bytes": 267.965952e6 + 13.033216e6, "src": "6896c6cfb12a8a61",
+    "tc_gemm_kernel": {"bytes": 268.139520e6 + 12.797440e6, "src": "68b725b7d111a547",
                        "files": ("tc_gemm.cu", "tc_gemm.cuh", "ptx.cuh", "nmf_internal.cuh"),
                        "scope": "finest-level V-step product, 256x256 grid n=2000 r=64"},
 }
