@@ -34,11 +34,11 @@
 namespace nmfk {
 namespace {
 
-constexpr int CT = 512;                      // threads per CTA
+constexpr int CT = 384;                      // threads per CTA
 constexpr int CW = 16;                       // columns of M_l per chunk
 constexpr int RS = 68;                       // row stride (floats) of rank-wide row buffers
 constexpr int QG = 8;                        // chunks per group of the fixed-order reduction
-constexpr int kMaxRows = CT / 4;             // rows a row update covers in one pass
+constexpr int kMaxRows = CT / 4;             // rows a row update covers in one pass (W^T rows per CTA)
 constexpr uint32_t kBarrierSpins = 1u << 20;
 constexpr size_t kMaxSmem = 232448;          // 227 KiB opt-in limit per block
 constexpr int kMaxVRows = 32;                // coarse runs only where V_l has at most this many rows
@@ -48,13 +48,6 @@ constexpr int kMaxVRows = 32;                // coarse runs only where V_l has a
 constexpr int GB = 20;
 constexpr int GS = 80;                       // floats per Gram row
 __host__ __device__ inline int gidx(int l, int c) { return l * GS + (c >> 4) * GB + (c & 15); }
-
-// Row ranges of V summed separately (then added in order) when forming D = V^T V;
-// with at most kMaxVRows rows one range is enough.
-__host__ __device__ inline int dparts(int r) {
-    (void)r;
-    return 1;
-}
 
 struct CLayout {
     size_t ms, ws, vs, ps, bs, ds, binv, dinv, scr, flag, total;
@@ -71,9 +64,7 @@ __host__ __device__ inline CLayout clayout(int m, int cpc, int r) {
     CLayout L;
     L.JS = CW * cpc;
     L.MS = L.JS + 4;
-    const int nq = (r + 3) / 4;
-    size_t scr = (size_t)dparts(r) * 16 * nq * nq;
-    if (scr < 4 * CT) scr = 4 * CT;
+    size_t scr = 4 * CT;
     if (scr < (size_t)4 * CW * 64) scr = (size_t)4 * CW * 64;
     size_t o = 0;
     L.ms = take_floats(o, (size_t)m * L.MS);
@@ -217,9 +208,10 @@ __device__ void reduce_slots(const CoarseParams& q, int e4_begin, int e4_count, 
 // row exists.
 // One step k = 16 q0 + i0 of the HALS walk (Algorithm 3): the thread that owns
 // block q0 updates entry i0 of its row, the delta is broadcast to the row's four
-// threads and each removes its contribution from its entries of g.
-__device__ __forceinline__ void hals_step(int k, int i0, int qd, int q0, int gbase, const float* G, float* f,
-                                          float* g, const float* gi) {
+// threads and each removes its contribution from its entries of g.  gk holds this
+// thread's 16 entries of Gram row k (loaded a step ahead).
+__device__ __forceinline__ void hals_step(int i0, int qd, int q0, int gbase, const float4* gk, float* f, float* g,
+                                          const float* gi) {
     float dl = 0.f;
     if (qd == q0) {
         const float nv = fmaxf(0.f, fmaf(g[i0], gi[i0], f[i0]));
@@ -227,14 +219,36 @@ __device__ __forceinline__ void hals_step(int k, int i0, int qd, int q0, int gba
         f[i0] = nv;
     }
     const float d = __shfl_sync(0xffffffffu, dl, gbase + q0);
-    const float4* gk = reinterpret_cast<const float4*>(G + k * GS + qd * GB);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        const float4 gv = gk[v];
-        g[4 * v] = fmaf(-d, gv.x, g[4 * v]);
-        g[4 * v + 1] = fmaf(-d, gv.y, g[4 * v + 1]);
-        g[4 * v + 2] = fmaf(-d, gv.z, g[4 * v + 2]);
-        g[4 * v + 3] = fmaf(-d, gv.w, g[4 * v + 3]);
+        g[4 * v] = fmaf(-d, gk[v].x, g[4 * v]);
+        g[4 * v + 1] = fmaf(-d, gk[v].y, g[4 * v + 1]);
+        g[4 * v + 2] = fmaf(-d, gk[v].z, g[4 * v + 2]);
+        g[4 * v + 3] = fmaf(-d, gk[v].w, g[4 * v + 3]);
+    }
+}
+
+// Steps k = 16 q0 .. 16 q0 + nb - 1 in order, the Gram row of step k + 1 loaded while
+// step k runs.
+template <bool FULL>
+__device__ __forceinline__ void hals_block(int q0, int nb, int qd, int gbase, const float* G, float* f, float* g,
+                                           const float* gi) {
+    float4 cur[4], nxt[4];
+    const float4* row0 = reinterpret_cast<const float4*>(G + (16 * q0) * GS + qd * GB);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) nxt[v] = row0[v];
+#pragma unroll
+    for (int i0 = 0; i0 < 16; ++i0) {
+        if (FULL || i0 < nb) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) cur[v] = nxt[v];
+            if (i0 + 1 < 16 && (FULL || i0 + 1 < nb)) {
+                const float4* rn = reinterpret_cast<const float4*>(G + (16 * q0 + i0 + 1) * GS + qd * GB);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) nxt[v] = rn[v];
+            }
+            hals_step(i0, qd, q0, gbase, cur, f, g, gi);
+        }
     }
 }
 
@@ -302,15 +316,8 @@ __device__ __noinline__ void quad_rows(int nrows, bool valid, float* F, const fl
         // k = 16 q0 + i0 in increasing order: full blocks without a per-step test,
         // then the last partial block
         const int full = r >> 4;
-        for (int q0 = 0; q0 < full; ++q0) {
-#pragma unroll
-            for (int i0 = 0; i0 < 16; ++i0) hals_step(16 * q0 + i0, i0, qd, q0, gbase, G, f, g, gi);
-        }
-        if (r & 15) {
-#pragma unroll
-            for (int i0 = 0; i0 < 16; ++i0)
-                if (16 * full + i0 < r) hals_step(16 * full + i0, i0, qd, full, gbase, G, f, g, gi);
-        }
+        for (int q0 = 0; q0 < full; ++q0) hals_block<true>(q0, 16, qd, gbase, G, f, g, gi);
+        if (r & 15) hals_block<false>(full, r & 15, qd, gbase, G, f, g, gi);
     }
     __syncwarp();  // the four threads of a row are done reading it
     if (act) {
@@ -382,8 +389,6 @@ __global__ void __launch_bounds__(CT, 1) coarse_run_kernel(const CoarseParams q)
     const int64_t wrow = (int64_t)(blockIdx.x + (wr / CW) * G) * CW + (wr % CW);
     const bool wvalid = wr < JS && wrow < q.n;
     const int nq = (r + 3) / 4;
-    const int NP = dparts(r);
-    const int per = (m + NP - 1) / NP;
     const int NPc = max(1, min(4, CT / (JS * 16)));
     const int perc = (m + NPc - 1) / NPc;
 
@@ -418,72 +423,55 @@ __global__ void __launch_bounds__(CT, 1) coarse_run_kernel(const CoarseParams q)
         __syncthreads();
         quad_rows<MODE>(m, true, Vs, Ps, Bs, binv, r);
         __syncthreads();
-        // D = V^T V: NP row ranges, 4 x 4 outputs per thread, ranges added in order
-        for (int t = tid; t < NP * nq * nq; t += CT) {
-            const int part = t / (nq * nq), rem = t % (nq * nq);
-            const int l4 = rem / nq, k4 = rem % nq;
-            const int i0 = part * per, i1 = min(m, i0 + per);
-            float a[4][4];
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-                for (int y = 0; y < 4; ++y) a[x][y] = 0.f;
-            for (int i = i0; i < i1; ++i) {
-                const float4 u = *reinterpret_cast<const float4*>(Vs + i * RS + 4 * l4);
-                const float4 v = *reinterpret_cast<const float4*>(Vs + i * RS + 4 * k4);
-                const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+        // ---- D = V^T V (4 x 4 outputs per item, rows of V in increasing order) and the
+        // W-step's products C = M_l^T V for this CTA's rows (NPc row ranges of V, added in
+        // order) in one pass: both only read V_l
+        const int nD = nq * nq, nC = NPc * JS * 16;
+        for (int t = tid; t < nD + nC; t += CT) {
+            if (t < nD) {
+                const int l4 = t / nq, k4 = t % nq;
+                float a[4][4];
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) a[x][y] = fmaf(uu[x], vv[y], a[x][y]);
-            }
-            if (NP == 1) {
+                    for (int y = 0; y < 4; ++y) a[x][y] = 0.f;
+                for (int i = 0; i < m; ++i) {
+                    const float4 u = *reinterpret_cast<const float4*>(Vs + i * RS + 4 * l4);
+                    const float4 v = *reinterpret_cast<const float4*>(Vs + i * RS + 4 * k4);
+                    const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) a[x][y] = fmaf(uu[x], vv[y], a[x][y]);
+                }
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
                     *reinterpret_cast<float4*>(Ds + gidx(4 * l4 + x, 4 * k4)) =
                         make_float4(a[x][0], a[x][1], a[x][2], a[x][3]);
             } else {
-                float* o = scr + (size_t)part * 16 * nq * nq;
-#pragma unroll
-                for (int x = 0; x < 4; ++x)
-                    *reinterpret_cast<float4*>(o + (4 * l4 + x) * 4 * nq + 4 * k4) =
-                        make_float4(a[x][0], a[x][1], a[x][2], a[x][3]);
-            }
-        }
-        __syncthreads();
-        if (NP > 1) {
-            for (int e = tid; e < 16 * nq * nq; e += CT) {
-                const int l = e / (4 * nq), k = e % (4 * nq);
-                float sum = scr[e];
-                for (int part = 1; part < NP; ++part) sum += scr[(size_t)part * 16 * nq * nq + e];
-                Ds[gidx(l, k)] = sum;
-            }
-            __syncthreads();
-        }
-        for (int k = tid; k < 64; k += CT) dinv[k] = (k < r && Ds[gidx(k, k)] > 0.f) ? 1.f / Ds[gidx(k, k)] : 0.f;
-
-        // ---- 4: W-step on this CTA's rows: C = M_l^T V (NPc row ranges of V, added in order)
-        for (int t = tid; t < NPc * JS * 16; t += CT) {
-            const int part = t / (JS * 16), rem = t % (JS * 16);
-            const int jr = rem / 16, k4 = rem % 16;
-            const int i0 = part * perc, i1 = min(m, i0 + perc);
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (k4 < nq4) {
-                for (int i = i0; i < i1; ++i) {
-                    const float a = Ms[i * MS + jr];
-                    const float4 v = *reinterpret_cast<const float4*>(Vs + i * RS + 4 * k4);
-                    acc.x = fmaf(a, v.x, acc.x);
-                    acc.y = fmaf(a, v.y, acc.y);
-                    acc.z = fmaf(a, v.z, acc.z);
-                    acc.w = fmaf(a, v.w, acc.w);
+                const int tc = t - nD;
+                const int part = tc / (JS * 16), rem = tc % (JS * 16);
+                const int jr = rem / 16, k4 = rem % 16;
+                const int i0 = part * perc, i1 = min(m, i0 + perc);
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k4 < nq4) {
+                    for (int i = i0; i < i1; ++i) {
+                        const float a = Ms[i * MS + jr];
+                        const float4 v = *reinterpret_cast<const float4*>(Vs + i * RS + 4 * k4);
+                        acc.x = fmaf(a, v.x, acc.x);
+                        acc.y = fmaf(a, v.y, acc.y);
+                        acc.z = fmaf(a, v.z, acc.z);
+                        acc.w = fmaf(a, v.w, acc.w);
+                    }
                 }
+                if (NPc == 1)
+                    *reinterpret_cast<float4*>(Ps + jr * RS + 4 * k4) = acc;
+                else
+                    *reinterpret_cast<float4*>(scr + (size_t)part * JS * 64 + jr * 64 + 4 * k4) = acc;
             }
-            if (NPc == 1)
-                *reinterpret_cast<float4*>(Ps + jr * RS + 4 * k4) = acc;
-            else
-                *reinterpret_cast<float4*>(scr + (size_t)part * JS * 64 + jr * 64 + 4 * k4) = acc;
         }
         __syncthreads();
+        for (int k = tid; k < 64; k += CT) dinv[k] = (k < r && Ds[gidx(k, k)] > 0.f) ? 1.f / Ds[gidx(k, k)] : 0.f;
         if (NPc > 1) {
             for (int e = tid; e < JS * 16; e += CT) {
                 const int jr = e / 16, k4 = e % 16;
@@ -492,8 +480,8 @@ __global__ void __launch_bounds__(CT, 1) coarse_run_kernel(const CoarseParams q)
                     sum = f4add(sum, *reinterpret_cast<const float4*>(scr + (size_t)part * JS * 64 + jr * 64 + 4 * k4));
                 *reinterpret_cast<float4*>(Ps + jr * RS + 4 * k4) = sum;
             }
-            __syncthreads();
         }
+        __syncthreads();
         quad_rows<MODE>(JS, wvalid, Ws, Ps, Ds, dinv, r);
         __syncthreads();
     }
