@@ -242,18 +242,25 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
         }
 
         bool capped = false;
+        // dual w = b - G x, recomputed only when x has changed: a candidate whose column
+        // depends on the passive set is excluded without changing x
+        double w[2] = {0.0, 0.0};
+        bool have_w = false;
         for (int outer = 0;; ++outer) {
-            // dual w = b - G x
-            double w[2] = {b[0], b[1]};
-            for (int l = 0; l < r; ++l) {
-                const double xl = __shfl_sync(kFull, x[l >> 5], l & 31);
-                if (xl != 0.0) {
+            if (!have_w) {
+                w[0] = b[0];
+                w[1] = b[1];
+                for (int l = 0; l < r; ++l) {
+                    const double xl = __shfl_sync(kFull, x[l >> 5], l & 31);
+                    if (xl != 0.0) {
 #pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const int k = lane + 32 * s;
-                        if (k < r) w[s] -= G[k * r + l] * xl;
+                        for (int s = 0; s < 2; ++s) {
+                            const int k = lane + 32 * s;
+                            if (k < r) w[s] -= G[k * r + l] * xl;
+                        }
                     }
                 }
+                have_w = true;
             }
             // entering variable: largest positive dual outside P (lowest index on ties)
             double best = -1.0;
@@ -285,6 +292,7 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
                 continue;
             }
             mask |= 1ull << j;
+            have_w = false;
             for (int it = 0; it <= r; ++it) {
                 chol_solve(L, dinv, r, ord, inv, p, mask, bs, z, y, lane);
                 uint64_t badm = 0;
