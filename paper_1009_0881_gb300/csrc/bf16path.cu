@@ -79,6 +79,11 @@ __global__ void gram_final_kernel(const float* __restrict__ slabs, int count, in
 }
 
 constexpr int TLD = BA + 1;  // row stride of the transposed tiles (odd: conflict-free columns)
+// G zero-padded to 64 x 64 for the HALS walk, row by row in four 16-column blocks
+// with block b at offset 20 b (row stride 80): the four 16-byte reads of a
+// quarter-warp (two rows, four blocks at the same offset) fall in distinct bank groups.
+constexpr int GBK = 20;
+constexpr int GRS = 4 * GBK;
 
 // HALS update (Algorithm HALS) of the BA = 64 rows of a tile, four lanes per row
 // (all 256 threads busy): lane q of a row's quad holds columns 16q .. 16q+15 of
@@ -86,7 +91,7 @@ constexpr int TLD = BA + 1;  // row stride of the transposed tiles (odd: conflic
 // order: the owner lane of column k computes F_ik <- max(0, F_ik + g_k / G_kk)
 // and broadcasts the change d within the quad, then every lane applies
 // g_j -= d G_kj to its sixteen columns (those at or before k are finished and
-// no longer read).  G64 is G zero-padded to 64 x 64; the loop over k is fully
+// no longer read).  G64 is G zero-padded to 64 x 64 (layout above); the loop over k is fully
 // unrolled so that every register index is static.  New rows go back to Fn
 // (row-major) and FT (transposed, for the BF16 copy).
 __device__ __forceinline__ void hals_rows_quad(int r, int rp, float* Fn, const float* Ared, const float* Dn,
@@ -128,7 +133,7 @@ __device__ __forceinline__ void hals_rows_quad(int r, int rp, float* Fn, const f
                     f[i0] = nv;
                 }
                 const float d = __shfl_sync(0xffffffffu, dl, gbase + q0);
-                const float4* gk = reinterpret_cast<const float4*>(G64 + k * kMaxRank + 16 * qd);
+                const float4* gk = reinterpret_cast<const float4*>(G64 + k * GRS + GBK * qd);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     const float4 gv = gk[v];
@@ -148,6 +153,48 @@ __device__ __forceinline__ void hals_rows_quad(int r, int rp, float* Fn, const f
     for (int j = 0; j < 16; ++j) FT[(16 * qd + j) * TLD + rr] = f[j];
 }
 
+// Dn = Fn G for the BA = 64 rows of a tile (Fn, Dn: rows of kMaxRank floats; G: r x rp):
+// thread (ty, tx) of a 16 x 16 arrangement computes columns 4tx .. 4tx+3 of rows
+// ty, ty+16, ty+32, ty+48, reading F four columns l at a time; each output is the sum
+// over l = 0 .. r-1 in increasing order (the order of rowupd::rows_times_gram).
+__device__ __forceinline__ void rows_times_gram64(int r, int rp, const float* Fn, const float* Gs, float* Dn) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int c0 = 4 * tx;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    if (c0 < rp) {
+        for (int l0 = 0; l0 < r; l0 += 4) {
+            float4 fv[4], gv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) fv[i] = *reinterpret_cast<const float4*>(Fn + (ty + 16 * i) * kMaxRank + l0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                gv[e] = l0 + e < r ? *reinterpret_cast<const float4*>(Gs + (l0 + e) * rp + c0)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float f[4] = {fv[i].x, fv[i].y, fv[i].z, fv[i].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (l0 + e < r) {
+                        acc[i][0] = fmaf(f[e], gv[e].x, acc[i][0]);
+                        acc[i][1] = fmaf(f[e], gv[e].y, acc[i][1]);
+                        acc[i][2] = fmaf(f[e], gv[e].z, acc[i][2]);
+                        acc[i][3] = fmaf(f[e], gv[e].w, acc[i][3]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(Dn + (ty + 16 * i) * kMaxRank + c0) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) {
     extern __shared__ __align__(16) float sm[];
@@ -158,9 +205,8 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
     float* Fn = Ginv + kMaxRank;          // BA x kMaxRank
     float* Ared = Fn + BA * kMaxRank;     // BA x kMaxRank
     float* Dn = Ared + BA * kMaxRank;     // BA x kMaxRank
-    float* Fg = Dn + BA * kMaxRank;       // r x rp
-    float* FT = Fg + r * rp;              // kMaxRank x TLD (HALS: new rows transposed)
-    float* G64 = FT + kMaxRank * TLD;     // kMaxRank x kMaxRank (HALS: G zero-padded)
+    float* FT = Dn + BA * kMaxRank;       // kMaxRank x TLD (HALS: new rows transposed)
+    float* G64 = FT + kMaxRank * TLD;     // kMaxRank x GRS (HALS: G zero-padded)
     const int tid = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * BA;
     const int R = BA;
@@ -198,12 +244,12 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
 
     if (MODE != rowupd::kModeStore) {
         for (int k = tid; k < kMaxRank; k += NT) Ginv[k] = (k < r && Gs[k * rp + k] > 0.f) ? 1.f / Gs[k * rp + k] : 0.f;
-        rowupd::rows_times_gram<4>(R, r, rp, Fn, Gs, Dn);
+        rows_times_gram64(r, rp, Fn, Gs, Dn);
         __syncthreads();
         if (MODE == rowupd::kModeHals) {
             for (int e = tid; e < kMaxRank * kMaxRank; e += NT) {
                 const int k = e / kMaxRank, j = e - k * kMaxRank;
-                G64[e] = (k < r && j < r) ? Gs[k * rp + j] : 0.f;
+                G64[k * GRS + (j >> 4) * GBK + (j & 15)] = (k < r && j < r) ? Gs[k * rp + j] : 0.f;
             }
             __syncthreads();
             hals_rows_quad(r, rp, Fn, Ared, Dn, FT, G64, Ginv);
@@ -263,8 +309,7 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
 }
 
 size_t rows_smem_bytes(int r, int rp) {
-    return sizeof(float) * ((size_t)2 * r * rp + kMaxRank + 3 * BA * kMaxRank + kMaxRank * TLD +
-                            kMaxRank * kMaxRank);
+    return sizeof(float) * ((size_t)r * rp + kMaxRank + 3 * BA * kMaxRank + kMaxRank * TLD + kMaxRank * GRS);
 }
 
 }  // namespace
