@@ -20,7 +20,6 @@ namespace {
 
 using rowupd::f4add;
 constexpr int NT = rowupd::NT;
-constexpr int BA = 64;
 
 __global__ void to_bf16_kernel(const float* __restrict__ in, int64_t ldi, int64_t rows, int64_t cols,
                                __nv_bfloat16* __restrict__ out, int64_t ldo) {
@@ -78,15 +77,17 @@ __global__ void gram_final_kernel(const float* __restrict__ slabs, int count, in
     if (threadIdx.x == 0) cnt[blockIdx.x] = 0;
 }
 
-constexpr int TLD = BA + 1;  // row stride of the transposed tiles (odd: conflict-free columns)
+// Row stride of the transposed tile of BA rows (odd: conflict-free columns).
+template <int BA>
+__host__ __device__ constexpr int tld() { return BA + 1; }
 // G zero-padded to 64 x 64 for the HALS walk, row by row in four 16-column blocks
 // with block b at offset 20 b (row stride 80): the four 16-byte reads of a
 // quarter-warp (two rows, four blocks at the same offset) fall in distinct bank groups.
 constexpr int GBK = 20;
 constexpr int GRS = 4 * GBK;
 
-// HALS update (Algorithm HALS) of the BA = 64 rows of a tile, four lanes per row
-// (all 256 threads busy): lane q of a row's quad holds columns 16q .. 16q+15 of
+// HALS update (Algorithm HALS) of the BA rows of a tile (64, 32 or 16), four lanes per row
+// (all 256 threads busy for 64 rows): lane q of a row's quad holds columns 16q .. 16q+15 of
 // F_i and of g = P_i - F_i G in registers.  Columns k = 0 .. r-1 are walked in
 // order: the owner lane of column k computes F_ik <- max(0, F_ik + g_k / G_kk)
 // and broadcasts the change d within the quad, then every lane applies
@@ -94,9 +95,12 @@ constexpr int GRS = 4 * GBK;
 // no longer read).  G64 is G zero-padded to 64 x 64 (layout above); the loop over k is fully
 // unrolled so that every register index is static.  New rows go back to Fn
 // (row-major) and FT (transposed, for the BF16 copy).
+template <int BA>
 __device__ __forceinline__ void hals_rows_quad(int r, int rp, float* Fn, const float* Ared, const float* Dn,
                                                float* FT, const float* G64, const float* Ginv) {
+    constexpr int TLD = tld<BA>();
     const int tid = threadIdx.x;
+    if (tid >= 4 * BA) return;  // whole warps: 4 BA is a multiple of 32
     const int rr = tid >> 2, qd = tid & 3;
     const int gbase = (tid & 31) & ~3;
     float f[16], g[16];
@@ -153,29 +157,30 @@ __device__ __forceinline__ void hals_rows_quad(int r, int rp, float* Fn, const f
     for (int j = 0; j < 16; ++j) FT[(16 * qd + j) * TLD + rr] = f[j];
 }
 
-// Dn = Fn G for the BA = 64 rows of a tile (Fn, Dn: rows of kMaxRank floats; G: r x rp):
+// Dn = Fn G for the 16 RPT rows of a tile (Fn, Dn: rows of kMaxRank floats; G: r x rp):
 // thread (ty, tx) of a 16 x 16 arrangement computes columns 4tx .. 4tx+3 of rows
-// ty, ty+16, ty+32, ty+48, reading F four columns l at a time; each output is the sum
+// ty, ty+16, ..., reading F four columns l at a time; each output is the sum
 // over l = 0 .. r-1 in increasing order (the order of rowupd::rows_times_gram).
+template <int RPT>
 __device__ __forceinline__ void rows_times_gram64(int r, int rp, const float* Fn, const float* Gs, float* Dn) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int c0 = 4 * tx;
-    float acc[4][4];
+    float acc[RPT][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RPT; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     if (c0 < rp) {
         for (int l0 = 0; l0 < r; l0 += 4) {
-            float4 fv[4], gv[4];
+            float4 fv[RPT], gv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) fv[i] = *reinterpret_cast<const float4*>(Fn + (ty + 16 * i) * kMaxRank + l0);
+            for (int i = 0; i < RPT; ++i) fv[i] = *reinterpret_cast<const float4*>(Fn + (ty + 16 * i) * kMaxRank + l0);
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 gv[e] = l0 + e < r ? *reinterpret_cast<const float4*>(Gs + (l0 + e) * rp + c0)
                                    : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < RPT; ++i) {
                 const float f[4] = {fv[i].x, fv[i].y, fv[i].z, fv[i].w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -190,13 +195,14 @@ __device__ __forceinline__ void rows_times_gram64(int r, int rp, const float* Fn
         }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RPT; ++i)
         *reinterpret_cast<float4*>(Dn + (ty + 16 * i) * kMaxRank + c0) =
             make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
 }
 
-template <int MODE>
+template <int MODE, int BA>
 __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) {
+    constexpr int TLD = tld<BA>();
     extern __shared__ __align__(16) float sm[];
     if (q.skip && *(volatile const int*)q.skip) return;  // converged problem: nothing to do
     const int r = q.r, rp = q.rp;
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
 
     if (MODE != rowupd::kModeStore) {
         for (int k = tid; k < kMaxRank; k += NT) Ginv[k] = (k < r && Gs[k * rp + k] > 0.f) ? 1.f / Gs[k * rp + k] : 0.f;
-        rows_times_gram64(r, rp, Fn, Gs, Dn);
+        rows_times_gram64<BA / 16>(r, rp, Fn, Gs, Dn);
         __syncthreads();
         if (MODE == rowupd::kModeHals) {
             for (int e = tid; e < kMaxRank * kMaxRank; e += NT) {
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
                 G64[k * GRS + (j >> 4) * GBK + (j & 15)] = (k < r && j < r) ? Gs[k * rp + j] : 0.f;
             }
             __syncthreads();
-            hals_rows_quad(r, rp, Fn, Ared, Dn, FT, G64, Ginv);
+            hals_rows_quad<BA>(r, rp, Fn, Ared, Dn, FT, G64, Ginv);
             __syncthreads();
             // new rows to the factor in global memory
             for (int e = tid; e < BA * Q4; e += NT) {
@@ -308,8 +314,8 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
     }
 }
 
-size_t rows_smem_bytes(int r, int rp) {
-    return sizeof(float) * ((size_t)r * rp + kMaxRank + 3 * BA * kMaxRank + kMaxRank * TLD + kMaxRank * GRS);
+size_t rows_smem_bytes(int r, int rp, int ba) {
+    return sizeof(float) * ((size_t)r * rp + kMaxRank + 3 * ba * kMaxRank + kMaxRank * (ba + 1) + kMaxRank * GRS);
 }
 
 }  // namespace
@@ -343,27 +349,47 @@ cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int
     return cudaGetLastError();
 }
 
-cudaError_t rows_update_init() {
-    const int maxs = (int)rows_smem_bytes(kMaxRank, kMaxRank);
-    cudaError_t e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeHals>,
+template <int BA>
+cudaError_t rows_update_init_ba() {
+    const int maxs = (int)rows_smem_bytes(kMaxRank, kMaxRank, BA);
+    cudaError_t e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeHals, BA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeMu>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeMu, BA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  maxs);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rows_update_kernel<rowupd::kModeStore, BA>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
     return e;
+}
+
+cudaError_t rows_update_init() {
+    cudaError_t e = rows_update_init_ba<64>();
+    if (e == cudaSuccess) e = rows_update_init_ba<32>();
+    return e == cudaSuccess ? rows_update_init_ba<16>() : e;
+}
+
+template <int BA>
+void rows_update_launch_ba(const RowsParams& q, int mode, cudaStream_t st) {
+    const size_t smem = rows_smem_bytes(q.r, q.rp, BA);
+    const unsigned grid = (unsigned)ceil_div(q.rows, BA);
+    switch (mode) {
+        case rowupd::kModeHals: rows_update_kernel<rowupd::kModeHals, BA><<<grid, NT, smem, st>>>(q); break;
+        case rowupd::kModeMu: rows_update_kernel<rowupd::kModeMu, BA><<<grid, NT, smem, st>>>(q); break;
+        default: rows_update_kernel<rowupd::kModeStore, BA><<<grid, NT, smem, st>>>(q); break;
+    }
 }
 
 cudaError_t rows_update_launch(const RowsParams& q, int mode, cudaStream_t st) {
     if (q.rows <= 0) return cudaSuccess;
-    const size_t smem = rows_smem_bytes(q.r, q.rp);
-    const unsigned grid = (unsigned)ceil_div(q.rows, BA);
-    switch (mode) {
-        case rowupd::kModeHals: rows_update_kernel<rowupd::kModeHals><<<grid, NT, smem, st>>>(q); break;
-        case rowupd::kModeMu: rows_update_kernel<rowupd::kModeMu><<<grid, NT, smem, st>>>(q); break;
-        default: rows_update_kernel<rowupd::kModeStore><<<grid, NT, smem, st>>>(q); break;
-    }
+    if (q.ba == 16)
+        rows_update_launch_ba<16>(q, mode, st);
+    else if (q.ba == 32)
+        rows_update_launch_ba<32>(q, mode, st);
+    else if (q.ba == 64)
+        rows_update_launch_ba<64>(q, mode, st);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -325,7 +325,7 @@ void layout(Plan& p, Bump& b, int num_sms) {
     p.gb_count = (int)ceil_div(n, p.wtile);
     // slab buffers sized for the smallest tile height, so that the autotuner can try
     // every candidate in place
-    const int min_tile = p.bf16 ? 64 : 16;
+    const int min_tile = 16;
     int max_gd = 1;
     for (int l = 0; l < p.L; ++l) {
         p.lv[l].gd_count = (int)ceil_div(p.lv[l].m, p.lv[l].vtile);
@@ -737,6 +737,16 @@ int make_plan(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, 
     return tune_plan(h, p);
 }
 
+// Rows per CTA of the BF16 form's row update: 64-row tiles, or 32 / 16 rows when 64-row
+// tiles would fill less than half / an eighth of the SMs (the W-step's n rows, coarse
+// levels).  Smaller tiles shorten a lone solve but add per-CTA work (the Gram matrix
+// loaded per CTA, one Gram slab per tile), which costs throughput when many problems
+// share the GPU.
+int bf16_tile(nmf_ctx* h, int64_t rows) {
+    const int64_t t64 = ceil_div(rows, 64);
+    return t64 >= h->num_sms / 2 ? 64 : (t64 >= h->num_sms / 8 ? 32 : 16);
+}
+
 void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r, int L, int64_t trace_cap,
                int max_ctas) {
     p.m = m;
@@ -747,9 +757,9 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
     p.br = pick_br(p.rp);
     // W-step tile height chosen on the finest level (the W-step tiles and their Gram
     // slabs are shared by all levels); V-step tiles per level.  The BF16 form's row
-    // update works on 64-row tiles.
+    // update works on 64-, 32- or 16-row tiles (bf16_tile).
     p.max_ctas = max_ctas > 0 ? std::min(max_ctas, h->num_sms) : h->num_sms;
-    p.wtile = p.bf16 ? 64 : choose_tile(h, p.br, r, n, p.max_ctas, nullptr);
+    p.wtile = p.bf16 ? bf16_tile(h, n) : choose_tile(h, p.br, r, n, p.max_ctas, nullptr);
     p.L = L;
     p.ldm = round_up(n, 4);
     p.trace_cap = trace_cap;
@@ -763,7 +773,7 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
         ww = (ww + 1) / 2;
     }
     for (int l = 0; l < L; ++l)
-        p.lv[l].vtile = p.bf16 ? 64 : choose_tile(h, p.br, r, p.lv[l].m, p.max_ctas, nullptr);
+        p.lv[l].vtile = p.bf16 ? bf16_tile(h, p.lv[l].m) : choose_tile(h, p.br, r, p.lv[l].m, p.max_ctas, nullptr);
     apply_tuned(h, p);
 }
 
@@ -909,6 +919,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
     q.Gout = p.GD;
     q.gout_stride = p.slab;
     q.skip = skip;
+    q.ba = v.vtile;
     if (algo == NMF_ANLS) {
         UpdateArgs u{};
         u.F = v.V;
@@ -939,6 +950,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
     q.Fb = p.Wb;
     q.ldb = p.ldmb;
     q.Gout = p.GB;
+    q.ba = p.wtile;
     if (algo == NMF_ANLS) {
         UpdateArgs u{};
         u.F = p.Wt;
@@ -1650,6 +1662,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                     q.Fb = vstep ? v.Vtb : p.Wb;
                     q.ldb = vstep ? v.ldmtb : p.ldmb;
                     q.Gout = vstep ? p.GD : p.GB;
+                    q.ba = vstep ? v.vtile : p.wtile;
                     q.gout_stride = p.slab;
                     if (e == cudaSuccess) e = rows_update_launch(q, mode == kModeStore ? 2 : mode, h->stream);
                     nl = 2;

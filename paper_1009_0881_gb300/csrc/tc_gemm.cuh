@@ -53,9 +53,10 @@ struct RowsParams {
     const float* G;        // final Gram matrix, r x rp
     __nv_bfloat16* Fb;     // transposed BF16 copy written after the update: Fb[k*ldb + row]
     int64_t ldb;
-    float* Gout;           // Gram slab of every 64-row tile of the new rows
+    float* Gout;           // Gram slab of every tile (ba rows) of the new rows
     int64_t gout_stride;
     const int* skip;       // optional: when *skip != 0 the launch does nothing
+    int ba;                // rows per CTA tile (64, 32 or 16): one Gram slab per tile
 };
 // mode: 0 HALS, 1 MU, 2 no update (copy + Gram slabs only)
 cudaError_t rows_update_launch(const RowsParams& q, int mode, cudaStream_t st);
