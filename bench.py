@@ -421,7 +421,7 @@ TRAFFIC = {
     "half_sweep_kernel": {"bytes": 0.5 * (4.968704e6 + 4.231936e6), "src": "a15ed2a98ec25cc9",
                           "files": ("fused.cu", "fused.cuh", "rowupdate.cuh", "ptx.cuh", "nmf_internal.cuh"),
                           "scope": "mean of the finest-level V-step (64-row tiles) and W-step (32-row tiles) launches, 19x19 grid n=2429 r=49"},
-    "tc_gemm_kernel": {"bytes": 268.139520e6 + 12.797440e6, "src": "68b725b7d111a547",
+    "tc_gemm_kernel": {"bytes": 267.958272e6 + 12.637184e6, "src": "ca1590c186c3c3bb",
                        "files": ("tc_gemm.cu", "tc_gemm.cuh", "ptx.cuh", "nmf_internal.cuh"),
                        "scope": "finest-level V-step product, 256x256 grid n=2000 r=64"},
 }
