@@ -140,23 +140,37 @@ __global__ void transpose_kernel(const float* __restrict__ in, int64_t ldi, int6
     }
 }
 
+__device__ __forceinline__ unsigned not_ok(float v) { return (!(v >= 0.f) || isinf(v)) ? 1u : 0u; }
+
+// Counts the entries of X (rows x cols, leading dimension ld) that are negative,
+// NaN or infinite.  A dense X is read as float4 over the whole array; a padded one
+// row by row, the threads of a block striding over the columns (no index division).
 __global__ void check_kernel(const float* __restrict__ X, int64_t ld, int64_t rows, int64_t cols,
                              unsigned long long* bad) {
     unsigned long long cnt = 0;
-    const int64_t total = rows * cols;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = t / cols, c = t - r * cols;
-        const float v = X[r * ld + c];
-        if (!(v >= 0.f) || isinf(v)) ++cnt;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (ld == cols) {
+        const int64_t total = rows * cols;
+        const int64_t n4 = (reinterpret_cast<uintptr_t>(X) % 16 == 0) ? total / 4 : 0;
+        const float4* X4 = reinterpret_cast<const float4*>(X);
+        for (int64_t t = gid; t < n4; t += stride) {
+            const float4 v = X4[t];
+            cnt += not_ok(v.x) + not_ok(v.y) + not_ok(v.z) + not_ok(v.w);
+        }
+        for (int64_t t = 4 * n4 + gid; t < total; t += stride) cnt += not_ok(X[t]);
+    } else {
+        for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+            for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) cnt += not_ok(X[r * ld + c]);
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(bad, cnt);
 }
 
 // ||M - V Wt^T||_F^2: each CTA owns a 64 x 64 tile of M, recomputes the tile
-// of V W from V (64 x r) and Wt (64 x r) in shared memory, and accumulates the
-// squared residuals in FP64; one partial per CTA.
+// of V W from V (64 x r) and Wt (64 x r) in shared memory, sums each thread's
+// squared residuals four at a time in FP32 and those sums in FP64; one partial
+// per CTA.
 constexpr int kErrTile = 64;
 
 __global__ void __launch_bounds__(256) error_tile_kernel(const float* __restrict__ M, int64_t ldm,
@@ -193,18 +207,22 @@ __global__ void __launch_bounds__(256) error_tile_kernel(const float* __restrict
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(va[a], wb[b], acc[a][b]);
     }
+    // the four squared residuals of a row in FP32 (at most 4 rounding steps), then the
+    // FP64 sum: GB300 runs FP64 at a small fraction of the FP32 rate
     double s = 0.0;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int64_t i = i0 + ty * 4 + a;
         if (i >= m) continue;
+        float sa = 0.f;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int64_t j = j0 + tx + 16 * b;
             if (j >= n) continue;
             const float e = M[i * ldm + j] - acc[a][b];
-            s += (double)e * (double)e;
+            sa = fmaf(e, e, sa);
         }
+        s += (double)sa;
     }
     __shared__ double red[256];
     red[threadIdx.x] = s;
