@@ -876,8 +876,10 @@ cudaError_t enqueue_hierarchy(nmf_ctx* h, const Plan& p) {
         const Level& c = p.lv[l + 1];
         cudaError_t e = restrict_launch(f.M, p.ldm, f.h, f.w, p.ldm, c.M, p.ldm, h->stream);
         if (e != cudaSuccess) return e;
-        e = copy2d_launch(c.M, p.ldm, c.m, p.n, c.Mt, c.ldmt, true, h->stream);
-        if (e != cudaSuccess) return e;
+        if (!p.bf16) {  // M^T: the FP32 V-step operand (the BF16 form reads its own BF16 copies)
+            e = copy2d_launch(c.M, p.ldm, c.m, p.n, c.Mt, c.ldmt, true, h->stream);
+            if (e != cudaSuccess) return e;
+        }
     }
     if (p.bf16) {
         // BF16 operand copies of every level (the objective stays on the FP32 M)
@@ -1074,13 +1076,19 @@ int check_dims(nmf_ctx* h, int64_t m, int64_t n, int r) {
 }
 
 // Stage M, V0, W0 into level 0 of the plan and validate them on the device.
-int stage_problem(nmf_ctx* h, Plan& p, const float* M, const float* V, const float* W) {
+// Copies the caller's M, V, W into the plan's buffers.  need_mt: also form M^T (the
+// operand of the FP32 V-step products; the BF16 form, the error and the coarse-run
+// kernel read M only).
+int stage_problem(nmf_ctx* h, Plan& p, const float* M, const float* V, const float* W, bool need_mt = true) {
     Level& f = p.lv[0];
     CK(stage_in(h, M, p.m, p.n, f.M, p.ldm));
-    KL(1, copy2d_launch(f.M, p.ldm, p.m, p.n, f.Mt, f.ldmt, true, h->stream));
-    if (f.ldmt != p.m) {
-        // zero the padding columns of Mt (rows of the transpose beyond m)
-        CK(cudaMemset2DAsync(f.Mt + p.m, sizeof(float) * f.ldmt, 0, sizeof(float) * (f.ldmt - p.m), p.n, h->stream));
+    if (need_mt) {
+        KL(1, copy2d_launch(f.M, p.ldm, p.m, p.n, f.Mt, f.ldmt, true, h->stream));
+        if (f.ldmt != p.m) {
+            // zero the padding columns of Mt (rows of the transpose beyond m)
+            CK(cudaMemset2DAsync(f.Mt + p.m, sizeof(float) * f.ldmt, 0, sizeof(float) * (f.ldmt - p.m), p.n,
+                                 h->stream));
+        }
     }
     if (V) CK(stage_in(h, V, p.m, p.r, f.V, p.rp));
     if (W) {
@@ -1100,7 +1108,7 @@ int init_levels_padding(nmf_ctx* h, Plan& p) {
     for (int l = 1; l < p.L; ++l) {
         Level& v = p.lv[l];
         CK(cudaMemsetAsync(v.M, 0, sizeof(float) * v.m * p.ldm, h->stream));
-        CK(cudaMemsetAsync(v.Mt, 0, sizeof(float) * p.n * v.ldmt, h->stream));
+        if (!p.bf16) CK(cudaMemsetAsync(v.Mt, 0, sizeof(float) * p.n * v.ldmt, h->stream));
         CK(cudaMemsetAsync(v.V, 0, sizeof(float) * v.m * p.rp, h->stream));
     }
     return NMF_OK;
@@ -1129,7 +1137,7 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     if (rc) return rc;
     rc = init_levels_padding(h, p);
     if (rc) return rc;
-    rc = stage_problem(h, p, M, V, W);
+    rc = stage_problem(h, p, M, V, W, !p.bf16);
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
@@ -1238,7 +1246,7 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
     for (int i = 0; i < count; ++i) {
         rc = init_levels_padding(h, plans[i]);
         if (rc) return rc;
-        rc = stage_problem(h, plans[i], probs[i].M, probs[i].V, probs[i].W);
+        rc = stage_problem(h, plans[i], probs[i].M, probs[i].V, probs[i].W, !plans[i].bf16);
         if (rc) return rc;
         Plan& p = plans[i];
         CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
@@ -1488,7 +1496,7 @@ int nmf_error(nmf_handle h, const float* M, const float* V, const float* W, int6
     Plan p;
     rc = make_plan(h, p, m, n, (int)m, 1, r, 1, 0);
     if (rc) return rc;
-    rc = stage_problem(h, p, M, V, W);
+    rc = stage_problem(h, p, M, V, W, false);
     if (rc) return rc;
     const Level& f = p.lv[0];
     KL(2, error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, m, n, r, p.err_part, p.err_out, h->stream));
@@ -1616,7 +1624,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
     Plan p;
     rc = make_plan(h, p, m, n, (int)m, 1, r, 1, 0);
     if (rc) return rc;
-    rc = stage_problem(h, p, M, V, W);
+    rc = stage_problem(h, p, M, V, W, !p.bf16);
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
@@ -1740,7 +1748,7 @@ int nmf_profile_coarse(nmf_handle h, const float* M, int64_t m, int64_t n, int r
     real.base = h->ws;
     real.cap = h->ws_cap;
     layout(p, real, h->num_sms);
-    rc = stage_problem(h, p, M, V, W);
+    rc = stage_problem(h, p, M, V, W, false);
     if (rc) return rc;
     CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
     cudaEvent_t e0, e1;
