@@ -181,9 +181,10 @@ int nmf_server_stats(nmf_server s, int64_t* queued, int64_t* running, int64_t* c
 void nmf_server_destroy(nmf_server s);
 
 /*
- * nmf_error - ||M - VW||_F (problem (NMF), Section 2) with float32 products and
- * FP64 accumulation of the squared residuals.  *err_out receives the value
- * (host pointer).
+ * nmf_error - ||M - VW||_F (problem (NMF), Section 2) with float32 products;
+ * each thread sums four squared residuals of a row in float32 and the
+ * accumulation of those sums is FP64.  *err_out receives the value (host
+ * pointer).
  */
 int nmf_error(nmf_handle h, const float* M, const float* V, const float* W,
               int64_t m, int64_t n, int r, double* err_out);

@@ -55,18 +55,22 @@ __global__ void __launch_bounds__(256) error_dense_tile_kernel(const float* __re
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(va[a], Ws[k][tx + 16 * b], acc[a][b]);
     }
+    // as the allocating error kernel: a thread's four squared residuals of a row in
+    // FP32, those sums in FP64
     double s = 0.0;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int64_t i = i0 + ty * 4 + a;
         if (i >= m) continue;
+        float sa = 0.f;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int64_t j = j0 + tx + 16 * b;
             if (j >= n) continue;
             const float e = M[i * n + j] - acc[a][b];
-            s += (double)e * (double)e;
+            sa = fmaf(e, e, sa);
         }
+        s += (double)sa;
     }
     __shared__ double red[256];
     red[threadIdx.x] = s;
