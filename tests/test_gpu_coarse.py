@@ -91,6 +91,22 @@ def test_coarse_cycle_matches_oracle_and_half_sweep_path(built, case):
         assert abs(f - f0) <= max(1e-3 * f, 1e-6 * mnorm)
 
 
+@pytest.mark.parametrize("cycle", ["fmg", "ni"])
+def test_coarse_runs_in_fmg_and_nested_cycles(built, cycle):
+    # FMG and nested iteration visit the 4 x 4 level of a 16 x 16 grid several times, with
+    # restrictions and prolongations of V between the coarse runs
+    case = (16, 16, 300, 10, 3, 12, "hals")
+    gh, gw, n, r, L, K, algo = case
+    p = synth.make_problem(gh, gw, n, r, sigma=1.0, data_seed=7)
+    V, W = _solve(p, case, coarse=True, cycle=cycle)
+    Vo, Wo = o.solve(p.M, gh, gw, p.V, p.W, algo, levels=L, K=K, cycle=cycle)
+    f, fo = o.objective(p.M, V, W), o.objective(p.M, Vo, Wo)
+    mnorm = float(np.linalg.norm(p.M.astype(np.float64)))
+    assert abs(f - fo) <= max(1e-4 * fo, 1e-6 * mnorm), (f, fo)
+    V0, W0 = _solve(p, case, coarse=False, cycle=cycle)
+    assert rel(V @ W, V0 @ W0) <= 1e-4
+
+
 def test_coarse_rank_above_coarse_pixels(built):
     # rank 64 on a 4 x 4 coarse grid: V^T V on that level has rank <= 16, so the W-step
     # there moves along directions the objective does not see, and the point a few fine
