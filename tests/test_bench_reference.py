@@ -9,9 +9,15 @@ import sys
 from conftest import ROOT
 
 
+def _run(extra_env=None, gpus=1):
+    env = dict(os.environ, **(extra_env or {}))
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                           "--warmup", "0", "--gpus", str(gpus)], capture_output=True, text=True, timeout=300,
+                          cwd=ROOT, env=env)
+
+
 def test_reference_arm_prints_one_contract_line():
-    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    res = _run()
     assert res.returncode == 0, res.stderr[-2000:]
     lines = [l for l in res.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1, res.stdout
@@ -28,3 +34,14 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_under_two_ranks():
+    # launched like the GPU arm with two ranks: rank 1 exits 0 without work, rank 0 prints the
+    # line with the same config as the GPU arm's (replicas)
+    r1 = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, gpus=2)
+    assert r1.returncode == 0 and not r1.stdout.strip()
+    r0 = _run({"RANK": "0", "WORLD_SIZE": "2", "LOCAL_RANK": "0"}, gpus=2)
+    assert r0.returncode == 0, r0.stderr[-2000:]
+    d = json.loads([l for l in r0.stdout.splitlines() if l.strip().startswith("{")][0])
+    assert d["n_gpus"] == 2 and d["config"]["parallelism"] == "replicas"
