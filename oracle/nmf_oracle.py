@@ -342,24 +342,36 @@ def vcycle(Ms, grids, V, W, algo: str, L: int, K: int, level: int = 0, hooks=Non
     return smooth(M, V, W, algo, K // 2, trace, level + 1)
 
 
-def nested_iteration(Ms, grids, V0, W0, algo: str, L: int, K: int, level: int = 0, trace=None):
-    """Algorithm NI: solve on the coarser level (K coarse sweeps), prolong, then floor(3K/4) sweeps."""
+def nested_iteration(Ms, grids, V0, W0, algo: str, L: int, K: int, level: int = 0, trace=None, hooks=None):
+    """Algorithm NI: solve on the coarser level (K coarse sweeps), prolong, then floor(3K/4) sweeps.
+
+    ``hooks`` (optional list) receives ("ni", level, Vc, W) with the coarse result that the
+    prolongation and the fine-level sweeps start from.
+    """
     M = Ms[level]
     if L == 1:
         return smooth(M, V0, W0, algo, K, trace, level + 1)
     Vc0 = restrict(V0, *grids[level])
-    Vc, W = nested_iteration(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace)
+    Vc, W = nested_iteration(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace, hooks)
+    if hooks is not None:
+        hooks.append(("ni", level, Vc.copy(), W.copy()))
     V = prolong(Vc, *grids[level + 1], *grids[level])
     return smooth(M, V, W, algo, (3 * K) // 4, trace, level + 1)
 
 
-def full_multigrid(Ms, grids, V0, W0, algo: str, L: int, K: int, level: int = 0, trace=None):
-    """Algorithm FMG: FMG on the coarser level (budget K), prolong, then a V-cycle with budget floor(3K/4)."""
+def full_multigrid(Ms, grids, V0, W0, algo: str, L: int, K: int, level: int = 0, trace=None, hooks=None):
+    """Algorithm FMG: FMG on the coarser level (budget K), prolong, then a V-cycle with budget floor(3K/4).
+
+    ``hooks`` (optional list) receives ("fmg", level, Vc, W) with the coarse result that the
+    prolongation and the V-cycle start from.
+    """
     M = Ms[level]
     if L == 1:
         return smooth(M, V0, W0, algo, K, trace, level + 1)
     Vc0 = restrict(V0, *grids[level])
-    Vc, W = full_multigrid(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace)
+    Vc, W = full_multigrid(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace, hooks)
+    if hooks is not None:
+        hooks.append(("fmg", level, Vc.copy(), W.copy()))
     V = prolong(Vc, *grids[level + 1], *grids[level])
     return vcycle(Ms, grids, V, W, algo, L, (3 * K) // 4, level, None, trace)
 

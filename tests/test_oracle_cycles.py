@@ -134,3 +134,52 @@ def test_anls_vcycle_independent_of_v_transfers():
     Vb, Wb = o.solve(p.M, 8, 8, np.zeros_like(p.V), p.W, "anls", levels=2, K=8)
     np.testing.assert_array_equal(Va, Vb)
     np.testing.assert_array_equal(Wa, Wb)
+
+
+def _bottom_up_problem():
+    p = synth.make_problem(9, 9, 30, 4, data_seed=11)
+    Ms = o.restrict_hierarchy(p.M, 9, 9, 3)
+    grids = o.grid_hierarchy(9, 9, 3)
+    return Ms, grids, p.V.astype(np.float64), p.W.astype(np.float64)
+
+
+@pytest.mark.parametrize("algo", ["hals", "mu"])
+def test_nested_iteration_data_flow(algo):
+    # Algorithm NI, rebuilt from the pinned pieces: the coarsest level solves from the
+    # restricted initial V, each finer level starts its floor(3K/4) sweeps from the
+    # prolongation of the coarser result, with the W that came out of it
+    Ms, grids, V0, W0 = _bottom_up_problem()
+    K = 8
+    hooks = []
+    V, W = o.nested_iteration(Ms, grids, V0, W0, algo, 3, K, hooks=hooks)
+    Vc2, Wc2 = o.smooth(Ms[2], o.restrict(o.restrict(V0, *grids[0]), *grids[1]), W0, algo, K)
+    V1, W1 = o.smooth(Ms[1], o.prolong(Vc2, *grids[2], *grids[1]), Wc2, algo, (3 * K) // 4)
+    Vf, Wf = o.smooth(Ms[0], o.prolong(V1, *grids[1], *grids[0]), W1, algo, (3 * K) // 4)
+    assert [(k, lvl) for k, lvl, _, _ in hooks] == [("ni", 1), ("ni", 0)]
+    np.testing.assert_array_equal(hooks[0][2], Vc2)
+    np.testing.assert_array_equal(hooks[0][3], Wc2)
+    np.testing.assert_array_equal(hooks[1][2], V1)
+    np.testing.assert_array_equal(hooks[1][3], W1)
+    np.testing.assert_array_equal(V, Vf)
+    np.testing.assert_array_equal(W, Wf)
+
+
+@pytest.mark.parametrize("algo", ["hals", "mu"])
+def test_fmg_data_flow(algo):
+    # Algorithm FMG, rebuilt from the pinned pieces: FMG on the coarser level from the
+    # restricted initial V (budget K), then a V-cycle over this level and the ones below
+    # with budget floor(3K/4), started from the prolongation of the coarse result
+    Ms, grids, V0, W0 = _bottom_up_problem()
+    K = 8
+    hooks = []
+    V, W = o.full_multigrid(Ms, grids, V0, W0, algo, 3, K, hooks=hooks)
+    Vc2, Wc2 = o.smooth(Ms[2], o.restrict(o.restrict(V0, *grids[0]), *grids[1]), W0, algo, K)
+    V1, W1 = o.vcycle(Ms, grids, o.prolong(Vc2, *grids[2], *grids[1]), Wc2, algo, 2, (3 * K) // 4, level=1)
+    Vf, Wf = o.vcycle(Ms, grids, o.prolong(V1, *grids[1], *grids[0]), W1, algo, 3, (3 * K) // 4, level=0)
+    assert [(k, lvl) for k, lvl, _, _ in hooks] == [("fmg", 1), ("fmg", 0)]
+    np.testing.assert_array_equal(hooks[0][2], Vc2)
+    np.testing.assert_array_equal(hooks[0][3], Wc2)
+    np.testing.assert_array_equal(hooks[1][2], V1)
+    np.testing.assert_array_equal(hooks[1][3], W1)
+    np.testing.assert_array_equal(V, Vf)
+    np.testing.assert_array_equal(W, Wf)

@@ -114,6 +114,44 @@ def _vcycle_coarsest_half(Ms, grids, V, W, algo, L, K, level=0, hooks=None, trac
     return o.smooth(M, V, W, algo, K // 2, trace, level + 1)
 
 
+def _ni_fine_from_v0(Ms, grids, V0, W0, algo, L, K, level=0, trace=None, hooks=None):
+    # fine-level sweeps start from the initial V instead of the prolonged coarse result
+    M = Ms[level]
+    if L == 1:
+        return o.smooth(M, V0, W0, algo, K, trace, level + 1)
+    Vc0 = o.restrict(V0, *grids[level])
+    Vc, W = _ni_fine_from_v0(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace, hooks)
+    if hooks is not None:
+        hooks.append(("ni", level, Vc.copy(), W.copy()))
+    o.prolong(Vc, *grids[level + 1], *grids[level])
+    return o.smooth(M, V0, W, algo, (3 * K) // 4, trace, level + 1)
+
+
+def _fmg_vcycle_from_v0(Ms, grids, V0, W0, algo, L, K, level=0, trace=None, hooks=None):
+    # the V-cycle after the coarse FMG starts from the initial V instead of P(V')
+    M = Ms[level]
+    if L == 1:
+        return o.smooth(M, V0, W0, algo, K, trace, level + 1)
+    Vc0 = o.restrict(V0, *grids[level])
+    Vc, W = _fmg_vcycle_from_v0(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace, hooks)
+    if hooks is not None:
+        hooks.append(("fmg", level, Vc.copy(), W.copy()))
+    return o.vcycle(Ms, grids, V0, W, algo, L, (3 * K) // 4, level, None, trace)
+
+
+def _fmg_coarse_w0(Ms, grids, V0, W0, algo, L, K, level=0, trace=None, hooks=None):
+    # the V-cycle gets the initial W instead of the W that left the coarse FMG
+    M = Ms[level]
+    if L == 1:
+        return o.smooth(M, V0, W0, algo, K, trace, level + 1)
+    Vc0 = o.restrict(V0, *grids[level])
+    Vc, W = _fmg_coarse_w0(Ms, grids, Vc0, W0, algo, L - 1, K, level + 1, trace, hooks)
+    if hooks is not None:
+        hooks.append(("fmg", level, Vc.copy(), W.copy()))
+    V = o.prolong(Vc, *grids[level + 1], *grids[level])
+    return o.vcycle(Ms, grids, V, W0, algo, L, (3 * K) // 4, level, None, trace)
+
+
 def _table1_checks():
     return [lambda row=row: tc.test_vcycle_sweep_allocation_matches_table1(row) for row in tc._table1_rows()]
 
@@ -142,6 +180,10 @@ MUTANTS = {
     "objective squared": ("objective", _objective_squared, [ts.test_objective_is_frobenius_norm_by_loops]),
     "V-cycle pre/post budgets swapped": ("vcycle", _vcycle_swapped_budget, [tc.test_vcycle_order_follows_algorithm]),
     "V-cycle coarsest level short": ("vcycle", _vcycle_coarsest_half, _table1_checks()),
+    "NI fine sweeps from V0": ("nested_iteration", _ni_fine_from_v0,
+                               [lambda: tc.test_nested_iteration_data_flow("hals")]),
+    "FMG V-cycle from V0": ("full_multigrid", _fmg_vcycle_from_v0, [lambda: tc.test_fmg_data_flow("hals")]),
+    "FMG V-cycle with the initial W": ("full_multigrid", _fmg_coarse_w0, [lambda: tc.test_fmg_data_flow("hals")]),
 }
 
 
