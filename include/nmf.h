@@ -241,6 +241,20 @@ int nmf_device_info(nmf_handle h, int* num_sms, const char** build_tag);
 int nmf_set_stream(nmf_handle h, void* stream);
 
 /*
+ * nmf_set_limits - bounds of the iterative and waiting parts of a solve on h.
+ *   nnls_max_exchanges: cap on the variables an ANLS active-set solve may add
+ *     to its passive set per row (Appendix A.2; the reading used here caps the
+ *     outer loop at 3r).  A row that reaches the cap keeps its last iterate
+ *     (feasible, >= 0) and the call returns NMF_ENOCONV.  < 0: the default 3r.
+ *   barrier_spins: polls of a grid-wide barrier in the persistent kernels
+ *     before it gives up; the kernel then leaves, the call returns NMF_ETIMEOUT
+ *     and the handle stays usable.  < 0: the default (about a second).
+ * Takes effect for later calls on h (cached CUDA graphs are dropped).  Small
+ * values exist to exercise those two failure paths.
+ */
+int nmf_set_limits(nmf_handle h, int nnls_max_exchanges, int64_t barrier_spins);
+
+/*
  * nmf_last_launch_count - number of kernels the last successful call on h
  * launched (graph kernel nodes included), or a negative nmf_status.
  */
@@ -279,8 +293,10 @@ int nmf_profile_coarse(nmf_handle h, const float* M, int64_t m, int64_t n, int r
  * of cudaMalloc/cudaFree.  It needs no handle and calls no cudaMalloc,
  * cudaFree or allocating library routine.
  *
- *   M (m x n), V (m x r), W (r x n): device pointers on the calling thread's
- *     current device, dense row-major float32 (the caller's layout, no copy).
+ *   M (m x n), V (m x r), W (r x n): device (or managed) pointers on the
+ *     calling thread's current device, dense row-major float32 (the caller's
+ *     layout, no copy); a host pointer or another device's memory gives
+ *     NMF_EINVAL.
  *   stream: cudaStream_t (as void*) to run on; NULL = the default stream.
  *   err_out: host pointer; receives the norm.  The call returns once it is written.
  *
@@ -290,14 +306,16 @@ int nmf_profile_coarse(nmf_handle h, const float* M, int64_t m, int64_t n, int r
  * exits.  Its capacity is 65536 tiles of 64 x 64 entries of M, i.e.
  * ceil(m/64) * ceil(n/64) <= 65536 (for example m = n = 16384); larger
  * problems are rejected with NMF_ETOOBIG before any work is queued.
- * The first call on each device looks the array's device address up
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any CUDA stream capture begins.
+ * Every call looks the array's device address up (cudaGetSymbolAddress, on
+ * the calling thread's current device); nothing is cached between calls, so a
+ * device reset leaves no stale address behind.  The first call on a device
+ * may load the library's device code there: make it before any CUDA stream
+ * capture begins.
  * All calls on a device share the array and each call overwrites what it
  * uses, so calls whose GPU work overlaps (different streams or threads at
  * the same time) race and can return wrong values: serialise them.
- * Returns NMF_OK, NMF_EINVAL (null pointer, m or n < 1, r outside 1..64),
- * NMF_ETOOBIG, or NMF_ECUDA.
+ * Returns NMF_OK, NMF_EINVAL (null or non-device pointer, m or n < 1, r
+ * outside 1..64), NMF_ETOOBIG, or NMF_ECUDA.
  */
 int nmf_error_noalloc(const float* M, const float* V, const float* W, int64_t m, int64_t n, int r,
                       void* stream, double* err_out);

@@ -39,7 +39,6 @@ constexpr int CW = 16;                       // columns of M_l per chunk
 constexpr int RS = 68;                       // row stride (floats) of rank-wide row buffers
 constexpr int QG = 8;                        // chunks per group of the fixed-order reduction
 constexpr int kMaxRows = CT / 4;             // rows a row update covers in one pass (W^T rows per CTA)
-constexpr uint32_t kBarrierSpins = 1u << 20;
 constexpr size_t kMaxSmem = 232448;          // 227 KiB opt-in limit per block
 constexpr int kMaxVRows = 32;                // coarse runs only where V_l has at most this many rows
 // Gram matrices in shared memory: 64 rows of four 16-column blocks, block b of a row
@@ -99,7 +98,7 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
 // waits until it reaches nb * gridDim.x.  The wait is bounded; on expiry (or when
 // another CTA has already given up) it raises err_flag and returns false in every
 // thread of the CTA, which then leaves the kernel.
-__device__ bool grid_sync(unsigned* bar, int* err_flag, unsigned nb, int* flag) {
+__device__ bool grid_sync(unsigned* bar, int* err_flag, unsigned nb, int* flag, uint32_t spins) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned target = nb * gridDim.x;
@@ -107,7 +106,7 @@ __device__ bool grid_sync(unsigned* bar, int* err_flag, unsigned nb, int* flag) 
         int ok = 1;
         for (uint32_t i = 0;; ++i) {
             if ((int)(ld_acquire_gpu(bar) - target) >= 0) break;
-            if (i >= kBarrierSpins || *(volatile int*)err_flag) {
+            if (i >= spins || *(volatile int*)err_flag) {
                 atomicExch(err_flag, 1);
                 ok = 0;
                 break;
@@ -395,9 +394,9 @@ __global__ void __launch_bounds__(CT, 1) coarse_run_kernel(const CoarseParams q)
     for (int s = 0; s < q.sweeps; ++s) {
         // ---- 1-2: A = M_l W^T and B = W W^T from the chunk partials
         chunk_partials(q, Ms, MS, Ws, true);
-        if (!grid_sync(q.bar, q.err_flag, ++nb, flag)) return;
+        if (!grid_sync(q.bar, q.err_flag, ++nb, flag, q.spins)) return;
         reduce_slots(q, 0, (m + r) * nq4, reinterpret_cast<float4*>(q.red), reinterpret_cast<float4*>(scr));
-        if (!grid_sync(q.bar, q.err_flag, ++nb, flag)) return;
+        if (!grid_sync(q.bar, q.err_flag, ++nb, flag, q.spins)) return;
 
         // ---- 3: V-step in every CTA
         // A rows into Ps, B into Bs (columns past rp zero); four loads in flight per thread
@@ -488,7 +487,7 @@ __global__ void __launch_bounds__(CT, 1) coarse_run_kernel(const CoarseParams q)
 
     // ---- B = W W^T of the final W into Bout; V_l and W^T back to global memory
     chunk_partials(q, Ms, MS, Ws, false);
-    if (!grid_sync(q.bar, q.err_flag, ++nb, flag)) return;
+    if (!grid_sync(q.bar, q.err_flag, ++nb, flag, q.spins)) return;
     reduce_slots(q, m * nq4, r * nq4, reinterpret_cast<float4*>(q.Bout), reinterpret_cast<float4*>(scr));
     for (int e = tid; e < JS * nq4; e += CT) {
         const int jr = e / nq4, k4 = e % nq4;

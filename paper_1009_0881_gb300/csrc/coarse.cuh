@@ -23,7 +23,11 @@ struct CoarseParams {
     float* Bout;          // r x rp: W W^T of the final W (the Gram input of the next V-step)
     unsigned* bar;        // grid-barrier counter, zero at launch (the launcher clears it)
     int* err_flag;        // set to 1 if a grid barrier gave up waiting
+    uint32_t spins;       // polls of a grid barrier before it gives up (kGridBarrierSpins by default)
 };
+
+// Default spin budget of a grid barrier (about a second of polling).
+constexpr uint32_t kGridBarrierSpins = 1u << 20;
 
 cudaError_t coarse_init();
 // Whether a level of m rows, n columns and rank r can run on at most `max_grid`

@@ -273,7 +273,9 @@ __global__ void __launch_bounds__(NT, 1)
                 for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
         __syncthreads();  // every thread is done with this slot
-        if (tid == 0 && s + NST < nst) {
+        // after a wait that gave up, the issuing thread queues no further copies (the
+        // stage it gave up on may still be in flight into this slot)
+        if (tid == 0 && ok && s + NST < nst) {
             ptx::mbar_arrive_expect_tx(&bar[slot], kStageBytes);
             ptx::tma_load_2d(Xs + slot * KS * BA, &tmX, &bar[slot], a0, (int)(k0 + (s + NST) * KS));
             ptx::tma_load_2d(Ys + slot * KS * BR, &tmY, &bar[slot], 0, (int)(k0 + (s + NST) * KS));

@@ -72,6 +72,7 @@ struct UpdateArgs {
     int64_t rows;
     int r;
     double* Gd;        // ANLS: r x r scratch receiving the FP64 sum of the Gram partials
+    int max_outer;     // ANLS: cap on the variables added per row (< 0: 3r, the default)
 };
 
 // ANLS: F rows = argmin_{x>=0} 1/2 x^T G x - p^T x, FP64 active set.  status: device int

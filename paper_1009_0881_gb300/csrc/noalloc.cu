@@ -7,21 +7,16 @@
 // shares it.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "nmf_internal.cuh"
 
 namespace {
 
 constexpr int kTile = 64;                        // 64 x 64 tile of M per CTA
 constexpr int64_t kMaxTiles = 65536;             // scratch capacity: 64 Ki tiles = 512 KiB of doubles
-constexpr int kMaxDevices = 64;
 
 // slots [0, kMaxTiles): one partial sum per tile; slot kMaxTiles: the result
 __device__ __align__(256) double g_error_scratch[kMaxTiles + 1];
 
-std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};  // device address of g_error_scratch, per device
 
 // Same arithmetic as the handle-based error kernel, reading the caller's dense
 // layouts directly: M (m x n), V (m x r), W (r x n), all row-major.
@@ -29,7 +24,9 @@ __global__ void __launch_bounds__(256) error_dense_tile_kernel(const float* __re
                                                                const float* __restrict__ V,
                                                                const float* __restrict__ W, int64_t m, int64_t n,
                                                                int r, double* __restrict__ partials) {
-    __shared__ float Vs[nmfk::kMaxRank][kTile + 4];
+    // rows of Vs are read as float4: 16-byte aligned base, row stride a multiple of 4 floats
+    __shared__ __align__(16) float Vs[nmfk::kMaxRank][kTile + 4];
+    static_assert((kTile + 4) % 4 == 0, "Vs rows must keep float4 alignment");
     __shared__ float Ws[nmfk::kMaxRank][kTile + 1];
     const int64_t ntj = (n + kTile - 1) / kTile;
     const int64_t ti = blockIdx.x / ntj, tj = blockIdx.x - ti * ntj;
@@ -96,22 +93,28 @@ __global__ void finish_kernel(const double* __restrict__ partials, int64_t count
     if (threadIdx.x == 0) *out = sqrt(red[0]);
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array on the calling thread's current device.
+// Looked up on every call (cheap once the module is loaded), so nothing stale
+// survives a device reset or a new primary context.
 cudaError_t scratch_address(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_error_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_error_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
+}
+
+// True if p is device (or managed) memory that the current device can address.
+bool on_current_device(const void* p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -122,6 +125,8 @@ extern "C" int nmf_error_noalloc(const float* M, const float* V, const float* W,
     if (m < 1 || n < 1 || r < 1 || r > nmfk::kMaxRank) return NMF_EINVAL;
     const int64_t tiles = ((m + kTile - 1) / kTile) * ((n + kTile - 1) / kTile);
     if (tiles > kMaxTiles) return NMF_ETOOBIG;
+    // the kernels read the caller's arrays in place: host pointers are rejected, not staged
+    if (!on_current_device(M) || !on_current_device(V) || !on_current_device(W)) return NMF_EINVAL;
     double* scratch = nullptr;
     if (scratch_address(&scratch) != cudaSuccess) {
         cudaGetLastError();

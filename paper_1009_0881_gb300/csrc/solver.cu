@@ -211,6 +211,8 @@ struct nmf_ctx {
     std::vector<cudaStream_t> branch_streams;  // capture branches of batched solves
     std::vector<cudaEvent_t> branch_events;
     std::map<int, std::vector<int>> active;    // co-resident clusters of size 1..16, per kernel shape
+    int nnls_cap = -1;                         // ANLS exchange cap per row (< 0: 3r)
+    uint32_t barrier_spins = kGridBarrierSpins;  // polls of a grid barrier before it gives up
 };
 
 namespace {
@@ -808,6 +810,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.rows = v.m;
         u.r = p.r;
         u.Gd = p.Gd;
+        u.max_outer = h->nnls_cap;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e == cudaSuccess) e = gram_tiles_launch(v.V, v.m, p.r, p.rp, v.vtile, p.GD, p.slab, h->stream);
         if (e != cudaSuccess) return e;
@@ -835,6 +838,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.rows = p.n;
         u.r = p.r;
         u.Gd = p.Gd;
+        u.max_outer = h->nnls_cap;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream);
         if (e != cudaSuccess) return e;
@@ -865,6 +869,7 @@ cudaError_t enqueue_coarse_run(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
     q.Bout = p.GB;
     q.bar = p.cbar;
     q.err_flag = p.err_flag;
+    q.spins = h->barrier_spins;
     return coarse_run_launch(q, algo == NMF_HALS ? 0 : 1, v.cgrid, v.csmem, h->stream);
 }
 
@@ -937,6 +942,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
         u.rows = v.m;
         u.r = p.r;
         u.Gd = p.Gd;
+        u.max_outer = h->nnls_cap;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e != cudaSuccess) return e;
     }
@@ -968,6 +974,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
         u.rows = p.n;
         u.r = p.r;
         u.Gd = p.Gd;
+        u.max_outer = h->nnls_cap;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e != cudaSuccess) return e;
     }
@@ -1607,6 +1614,15 @@ int nmf_set_stream(nmf_handle h, void* stream) {
     return NMF_OK;
 }
 
+int nmf_set_limits(nmf_handle h, int nnls_max_exchanges, int64_t barrier_spins) {
+    if (!h) return NMF_EINVAL;
+    if (barrier_spins > (int64_t)UINT32_MAX) return fail(h, NMF_EINVAL, "barrier_spins must be below 2^32");
+    h->nnls_cap = nnls_max_exchanges < 0 ? -1 : nnls_max_exchanges;
+    h->barrier_spins = barrier_spins < 0 ? kGridBarrierSpins : (uint32_t)barrier_spins;
+    drop_graphs(h);  // recorded graphs carry the old limits in their kernel arguments
+    return NMF_OK;
+}
+
 int64_t nmf_last_launch_count(nmf_handle h) {
     if (!h) return NMF_EINVAL;
     return h->launches;
@@ -1697,6 +1713,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                     u.rows = vstep ? v.m : p.n;
                     u.r = p.r;
                     u.Gd = p.Gd;
+                    u.max_outer = h->nnls_cap;
                     e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
                     if (e == cudaSuccess)
                         e = gram_tiles_launch(u.F, u.rows, p.r, p.rp, vstep ? v.vtile : p.wtile, vstep ? p.GD : p.GB,

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
                 j = min(j, __shfl_sync(kFull, bestk, ln));
             }
             j = __shfl_sync(kFull, j, 0);
-            if (outer >= 3 * r) {
+            if (outer >= (u.max_outer < 0 ? 3 * r : u.max_outer)) {
                 capped = true;
                 break;
             }

@@ -17,6 +17,7 @@ from . import build as _build
 NMF_HALS, NMF_MU, NMF_ANLS = 0, 1, 2
 NMF_FP32, NMF_BF16 = 0, 1
 NMF_VCYCLE, NMF_NESTED, NMF_FMG = 0, 1, 2
+NMF_OK, NMF_EINVAL, NMF_ENOMEM, NMF_ENOCONV, NMF_ECUDA, NMF_ETIMEOUT, NMF_EBUSY, NMF_ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 ALGOS = {"hals": NMF_HALS, "mu": NMF_MU, "anls": NMF_ANLS}
 CYCLES = {"vcycle": NMF_VCYCLE, "ni": NMF_NESTED, "fmg": NMF_FMG}
 
@@ -42,6 +43,7 @@ SIGNATURES = [
     ("nmf_device_info", _I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_char_p)]),
     ("nmf_set_stream", _I, [_P, _P]),
     ("nmf_last_launch_count", _I64, [_P]),
+    ("nmf_set_limits", _I, [_P, _I, _I64]),
     ("nmf_profile_sweep", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
     ("nmf_profile_coarse", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
     ("nmf_error_noalloc", _I, [_P, _P, _P, _I64, _I64, _I, _P, ctypes.POINTER(ctypes.c_double)]),
@@ -258,6 +260,10 @@ class Handle:
     def set_stream(self, stream_ptr: int | None):
         """nmf_set_stream: run on the given cudaStream_t (an int address), None = own stream."""
         self._rc(self.lib.nmf_set_stream(self.h, stream_ptr or None))
+
+    def set_limits(self, nnls_max_exchanges: int = -1, barrier_spins: int = -1):
+        """nmf_set_limits: ANLS exchange cap and grid-barrier spin budget (-1 = defaults)."""
+        self._rc(self.lib.nmf_set_limits(self.h, int(nnls_max_exchanges), int(barrier_spins)))
 
     def last_launch_count(self) -> int:
         return int(self.lib.nmf_last_launch_count(self.h))

@@ -25,6 +25,15 @@ CASES = [
     ("grid19_mu_L3_K500", "grid19_n2429_r49", "mu", 3, 500, "vcycle"),
     ("grid19_mu_L1_K500", "grid19_n2429_r49", "mu", 1, 500, "vcycle"),
     ("grid19_anls_L2_K8", "grid19_n2429_r49", "anls", 2, 8, "vcycle"),
+    # the headline workload's ANLS, NI and FMG at three levels (the 5 x 5 level has m_l = 25 < r:
+    # its iterates are not unique, only the objective is compared)
+    ("grid19_anls_L3_K8", "grid19_n2429_r49", "anls", 3, 8, "vcycle"),
+    ("grid19_anls_L3_K500", "grid19_n2429_r49", "anls", 3, 500, "vcycle"),
+    ("grid19_anls_L1_K500", "grid19_n2429_r49", "anls", 1, 500, "vcycle"),
+    ("grid19_hals_fmg_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "fmg"),
+    ("grid19_hals_ni_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "ni"),
+    ("grid19_mu_fmg_L3_K100", "grid19_n2429_r49", "mu", 3, 100, "fmg"),
+    ("grid19_anls_fmg_L3_K8", "grid19_n2429_r49", "anls", 3, 8, "fmg"),
     # full multigrid and nested iteration start on the coarsest level: keep m_l >= r there
     ("grid19_hals_fmg_L2_K100", "grid19_n2429_r49", "hals", 2, 100, "fmg"),
     ("grid19_hals_ni_L2_K100", "grid19_n2429_r49", "hals", 2, 100, "ni"),
@@ -38,9 +47,20 @@ CASES = [
 ]
 
 
+def _store(path, name, entry):
+    """Merge one entry into the JSON file (several writers may run at once)."""
+    import fcntl
+    with open(path + ".lock", "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        out = json.load(open(path)) if os.path.exists(path) else {}
+        out[name] = entry
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1, sort_keys=True)
+            f.write("\n")
+
+
 def main(only=None):
     path = os.path.join(HERE, "objectives.json")
-    out = json.load(open(path)) if os.path.exists(path) else {}
     for name, wl, algo, L, K, cyc in CASES:
         if only and name not in only:
             continue
@@ -49,10 +69,9 @@ def main(only=None):
         t = time.time()
         V, W = o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc)
         f = o.objective(p.M.astype(np.float64), V, W)
-        out[name] = {"workload": wl, "algo": algo, "levels": L, "K": K, "cycle": cyc, "objective": f,
-                     "norm_M": float(np.linalg.norm(p.M.astype(np.float64)))}
+        _store(path, name, {"workload": wl, "algo": algo, "levels": L, "K": K, "cycle": cyc, "objective": f,
+                            "norm_M": float(np.linalg.norm(p.M.astype(np.float64)))})
         print(f"{name}: {f:.10g} ({time.time() - t:.1f} s)", flush=True)
-        json.dump(out, open(path, "w"), indent=1, sort_keys=True)
 
 
 if __name__ == "__main__":

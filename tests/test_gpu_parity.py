@@ -133,14 +133,43 @@ def test_single_sweep_matches_oracle(h, algo, case):
         assert abs(o.objective(M64, V, W) - fo) <= 1e-5 * fo
 
 
-@pytest.mark.parametrize("case", [("grid16_n1000_r10", None), (None, (8, 8, 37, 1)), (None, (9, 7, 130, 12))])
+def _support_condition(G, X):
+    """Largest 2-norm condition number of G restricted to the support of a row of X."""
+    worst = 1.0
+    for row in X:
+        P = np.flatnonzero(row > 0)
+        if len(P) > 1:
+            worst = max(worst, float(np.linalg.cond(G[np.ix_(P, P)])))
+    return worst
+
+
+@pytest.mark.parametrize("case", [("grid16_n1000_r10", None), (None, (8, 8, 37, 1)), (None, (9, 7, 130, 12)),
+                                  ("grid19_n2429_r49", None)])
 def test_single_anls_sweep_matches_oracle(h, case):
+    # An exact NNLS step (Appendix A.2) maps a perturbation of its data to the solution
+    # through the inverse of G restricted to the solution's support.  The GPU forms the
+    # products in float32 (relative rounding ~ 2^-24 sqrt(K) for K-term sums of
+    # nonnegative terms) and solves in FP64, so the bar for each half is
+    #     max(1e-5, 4 kappa (delta_products + incoming error)),
+    # kappa the worst condition number of G over the rows' supports at the oracle's solution.
     p = _problem(case)
     V, W = p.V.copy(), p.W.copy()
     h.sweep(p.M, V, W, "anls", 1)
-    Vo, Wo = o.anls_sweep(p.M.astype(np.float64), p.V.astype(np.float64), p.W.astype(np.float64))
-    assert rel(V, Vo) < 1e-4
-    assert rel(W, Wo) < 1e-4
+    M64 = p.M.astype(np.float64)
+    W0 = p.W.astype(np.float64)
+    Vo, Wo = o.anls_sweep(M64, p.V.astype(np.float64), W0)
+    m, n = p.M.shape
+    u = 2.0 ** -24
+    kv = _support_condition(W0 @ W0.T, Vo)
+    bar_v = max(1e-5, 4 * kv * u * np.sqrt(n))
+    ev = rel(V, Vo)
+    assert ev <= bar_v, (ev, bar_v, kv)
+    kw = _support_condition(Vo.T @ Vo, Wo.T)
+    bar_w = max(1e-5, 4 * kw * (u * np.sqrt(m) + ev))
+    ew = rel(W, Wo)
+    assert ew <= bar_w, (ew, bar_w, kw)
+    print(f"ANLS sweep {p.M.shape} r={p.V.shape[1]}: V {ev:.2e} (bar {bar_v:.2e}, kappa {kv:.3g}); "
+          f"W {ew:.2e} (bar {bar_w:.2e}, kappa {kw:.3g})")
 
 
 def test_hals_ten_sweeps_track_oracle(h):
@@ -187,6 +216,52 @@ def test_cycle_final_objective_matches_oracle(h, name):
     assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
     # the library's own error kernel agrees with the oracle's objective of the same iterate
     assert abs(h.error(p.M, V, W) - f) <= 1e-6 * f
+
+
+# The headline 19 x 19 workload at three levels with every algorithm and cycle.  Its coarsest
+# level has m_l = 25 < r = 49, where V is not unique; only the objective is compared
+# (1e-3 relative, as for every cycle), and the coarse-level ANLS results are checked for
+# the optimality conditions below instead.
+HEADLINE_L3 = ["grid19_anls_L3_K8", "grid19_anls_L3_K500", "grid19_anls_L1_K500", "grid19_anls_fmg_L3_K8",
+               "grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100", "grid19_mu_fmg_L3_K100"]
+
+
+@pytest.mark.parametrize("name", HEADLINE_L3)
+def test_headline_cycles_at_three_levels_match_oracle(h, name):
+    test_cycle_final_objective_matches_oracle(h, name)
+
+
+def _kkt_violation(G, B, X):
+    """Largest violation of the NNLS optimality conditions of min 1/2 x^T G x - b^T x, x >= 0,
+    over the rows x of X (rows b of B), relative to |G| |x| + |b|: the dual w = b - G x must be
+    <= 0 where x = 0 and = 0 where x > 0 (Appendix A.2)."""
+    worst = 0.0
+    for x, b in zip(X, B):
+        w = b - G @ x
+        scale = np.abs(G) @ np.abs(x) + np.abs(b) + 1e-300
+        v = np.where(x > 0, np.abs(w), np.maximum(w, 0.0)) / scale
+        worst = max(worst, float(v.max()))
+    return worst
+
+
+def test_anls_coarse_level_satisfies_kkt(h):
+    # the 5 x 5 level of the headline hierarchy: m = 25 < r = 49, so W W^T is regular but
+    # V^T V is singular and the W-step solution is not unique; every row must still be an
+    # optimal NNLS solution of its own data, up to float32 rounding of the products
+    gh, gw, n, r, sigma = synth.WORKLOADS["grid19_n2429_r49"]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    Ms = o.restrict_hierarchy(p.M, gh, gw, 3)
+    Mc = Ms[2].astype(np.float32)
+    V = np.asarray(o.restrict(o.restrict(p.V, gh, gw), 10, 10), np.float32)
+    W0 = p.W.copy()
+    W = W0.copy()
+    h.sweep(Mc, V, W, "anls", 1)
+    assert (V >= 0).all() and (W >= 0).all()
+    M64, V64, W064, W64 = Mc.astype(np.float64), V.astype(np.float64), W0.astype(np.float64), W.astype(np.float64)
+    # V-step data: G = W0 W0^T, rows of M W0^T; W-step data: G = V^T V, columns of V^T M
+    kv = _kkt_violation(W064 @ W064.T, M64 @ W064.T, V64)
+    kw = _kkt_violation(V64.T @ V64, (V64.T @ M64).T, W64.T)
+    assert kv <= 1e-5 and kw <= 1e-5, (kv, kw)
 
 
 def test_host_and_device_pointers_agree(h):

@@ -9,6 +9,7 @@ a failure here leaves every other test already run.
 import numpy as np
 import pytest
 
+from oracle import nmf_oracle as o
 from paper_1009_0881_gb300 import native, synth
 
 pytestmark = pytest.mark.gpu
@@ -41,6 +42,9 @@ def test_noalloc_matches_nmf_error_on_two_calls_in_a_row(handle):
         got = native.error_noalloc(M, V, W)
         ref = handle.error(M, V, W)
         assert abs(got - ref) <= 1e-6 * ref, (got, ref)
+        # and against the FP64 definition of the norm (problem (NMF), Section 2)
+        exact = o.objective(M.cpu().numpy(), V.cpu().numpy(), W.cpu().numpy())
+        assert abs(got - exact) <= 1e-6 * exact, (got, exact)
     # and once more on a caller-chosen stream
     s = torch.cuda.Stream()
     M, V, W = cases[0]
@@ -59,3 +63,18 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert rc == -7 and out.value == -1.0
     rc = lib.nmf_error_noalloc(x.data_ptr(), x.data_ptr(), x.data_ptr(), 8, 8, 65, None, ctypes.byref(out))
     assert rc == -1
+
+
+def test_noalloc_rejects_host_pointers():
+    import ctypes
+    import torch
+    x = torch.zeros(64, device="cuda")
+    h = np.zeros(64, np.float32)
+    lib = native.load()
+    out = ctypes.c_double(-1.0)
+    hp = h.ctypes.data
+    # the kernels read the arrays in place, so host memory is refused instead of staged
+    rc = lib.nmf_error_noalloc(hp, x.data_ptr(), x.data_ptr(), 8, 8, 1, None, ctypes.byref(out))
+    assert rc == -1 and out.value == -1.0
+    rc = lib.nmf_error_noalloc(x.data_ptr(), x.data_ptr(), hp, 8, 8, 1, None, ctypes.byref(out))
+    assert rc == -1 and out.value == -1.0
