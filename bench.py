@@ -86,27 +86,55 @@ def _schedule_py(L, K):
     return counts
 
 
-def workload_config(args, world=1):
-    """The `config` object of the bench line (both arms)."""
+def workload_config(args, world=1, iters=None, gpu=True):
+    """The `config` object of a bench line: the workload each step runs (iters = the sweep
+    budget K actually run; the GPU arm also states how L2 is flushed between steps)."""
     from paper_1009_0881_gb300 import synth
 
+    K = args.iters if iters is None else iters
     gh, gw, n, r, _ = synth.WORKLOADS[args.workload]
-    sched = _schedule_py(args.levels, args.iters)
-    return {"workload": f"{args.workload}: {gh}x{gw} grid, m={gh * gw}, n={n}, r={r}; {args.algo} V-cycle "
-                        f"L={args.levels} K={args.iters} ({sum(sched)} sweeps) + final error",
-            "algo": args.algo, "levels": args.levels, "iters": args.iters,
-            "sweeps_per_step": sum(sched), "sweeps_per_level": sched,
-            "l2": "inputs (3.5 MB) fit in L2: a 258 MB buffer is written between timed steps",
-            "parallelism": "replicas" if world > 1 else "single GPU"}
+    sched = _schedule_py(args.levels, K)
+    cfg = {"workload": f"{args.workload}: {gh}x{gw} grid, m={gh * gw}, n={n}, r={r}; {args.algo} V-cycle "
+                       f"L={args.levels} K={K} ({sum(sched)} sweeps) + final error",
+           "algo": args.algo, "levels": args.levels, "iters": K,
+           "sweeps_per_step": sum(sched), "sweeps_per_level": sched,
+           "parallelism": "replicas" if world > 1 else "single GPU"}
+    if gpu:
+        cfg["l2"] = "inputs (3.5 MB) fit in L2: a 258 MB buffer is written between timed steps"
+    return cfg
 
 
-def run_oracle_sample(args, K=None, levels=None):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+def run_oracle_sample(args, K=None, levels=None, threads=1):
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--_oracle_sample", "--workload", args.workload, "--algo",
            args.algo, "--levels", str(levels or args.levels), "--iters", str(K or args.iters)]
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True).stdout.strip().splitlines()[-1]
     return json.loads(out)
+
+
+# sweep budget K of one reference-arm step (a bounded sample of the K = 500 workload)
+REFERENCE_ITERS = 40
+
+
+def host_cpu():
+    """CPU model and logical core count of this host (for the CPU-baseline records)."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+            else:
+                f.seek(0)
+                for line in f:
+                    if line.startswith("CPU part"):
+                        model = "Arm CPU part " + line.split(":", 1)[1].strip()
+                        break
+    except OSError:
+        pass
+    return f"{model}, nproc {os.cpu_count()}"
 
 
 def reference_arm(args):
@@ -116,20 +144,20 @@ def reference_arm(args):
         return
     samples = []
     for _ in range(args.warmup):
-        run_oracle_sample(args, K=40)
+        run_oracle_sample(args, K=REFERENCE_ITERS)
     for _ in range(args.steps):
-        samples.append(run_oracle_sample(args, K=40))
+        samples.append(run_oracle_sample(args, K=REFERENCE_ITERS))
     sweeps = sum(s["sweeps"] for s in samples)
     secs = sum(s["seconds"] for s in samples)
     value = sweeps / secs
     desc = (f"FP64 numpy oracle, single thread; each step a bounded sample of the workload: {args.workload} "
-            f"{args.algo} V-cycle L={args.levels} with K=40 ({samples[0]['sweeps']} sweeps) instead of "
-            f"K={args.iters}, throughput in sweeps/s")
+            f"{args.algo} V-cycle L={args.levels} with K={REFERENCE_ITERS} ({samples[0]['sweeps']} sweeps) instead "
+            f"of K={args.iters}, throughput in sweeps/s; host {host_cpu()}")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, world),
+        "config": workload_config(args, world, iters=REFERENCE_ITERS, gpu=False),
         "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -209,9 +237,15 @@ def main_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = run_oracle_sample(args)
+        ncores = os.cpu_count() or 1
+        sa = run_oracle_sample(args, threads=ncores)
         cpu = {"value": s["sweeps"] / s["seconds"], "unit": "sweeps/s", "cores": 1, "kind": "oracle",
                "sample": (f"the whole step once: FP64 numpy oracle, one thread, {args.workload} {args.algo} "
-                          f"V-cycle L={args.levels} K={args.iters} ({s['sweeps']} sweeps in {s['seconds']:.1f} s)")}
+                          f"V-cycle L={args.levels} K={args.iters} ({s['sweeps']} sweeps in {s['seconds']:.1f} s)"),
+               "host": host_cpu(),
+               "all_cores": {"value": sa["sweeps"] / sa["seconds"], "unit": "sweeps/s", "cores": ncores,
+                             "sample": (f"the same step with numpy's BLAS on all {ncores} host threads "
+                                        f"({sa['sweeps']} sweeps in {sa['seconds']:.1f} s)")}}
 
     from paper_1009_0881_gb300 import build
     build.build()

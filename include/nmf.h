@@ -55,7 +55,9 @@ typedef enum {
 typedef enum {
     NMF_VCYCLE = 0, /* Algorithm V-cycle (Section 4.3.2) */
     NMF_NESTED = 1, /* Algorithm Nested Iteration (Section 4.3.1) */
-    NMF_FMG = 2     /* Algorithm Full Multigrid (Section 4.3.3) */
+    NMF_FMG = 2,    /* Algorithm Full Multigrid (Section 4.3.3) */
+    NMF_WCYCLE = 3  /* W-cycle (a grid cycle Section 7 names as an extension): the V-cycle with the
+                       coarser level visited twice in a row, each visit with sweep budget K/2 */
 } nmf_cycle;
 
 typedef enum {
@@ -193,7 +195,8 @@ int nmf_error(nmf_handle h, const float* M, const float* V, const float* W,
  * nmf_schedule - host-side sweep allocation of a cycle (no device work).
  *   Writes the number of sweeps run on each level 1..levels into
  *   sweeps_per_level[0..levels-1] (Table 1 of Section 4.3 for the V-cycle and
- *   nested iteration; Algorithm FMG's recursion for NMF_FMG) and returns the
+ *   nested iteration; Algorithm FMG's recursion for NMF_FMG; for NMF_WCYCLE two
+ *   coarser visits of budget K/2 in place of the V-cycle's one) and returns the
  *   total, or a negative nmf_status.
  */
 int64_t nmf_schedule(nmf_cycle cycle, int levels, int iters, int64_t* sweeps_per_level);

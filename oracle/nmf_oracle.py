@@ -168,6 +168,27 @@ def objective_sq_expanded(M: np.ndarray, V: np.ndarray, W: np.ndarray) -> float:
 
 
 # ---------------------------------------------------------------------------
+# The four products of a sweep (Appendix A.1): A = M W^T, B = W W^T, C = V^T M,
+# D = V^T V.  FP64 by default.  READING: cycles that start on a level with fewer
+# pixels than the rank (nested iteration and full multigrid on the 19 x 19 grid
+# with three levels: 25 pixels, r = 49) have a flat objective there, and the point
+# their sweeps settle on depends on how the products are rounded; with
+# PRODUCT_ROUNDING = np.float32 the operands and the results of these products are
+# rounded to float32 (everything else stays FP64), which states that case at the
+# precision of a float32 implementation.  solve(..., products="fp32") sets it.
+# ---------------------------------------------------------------------------
+PRODUCT_ROUNDING = None
+
+
+def product(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """X @ Y in FP64, or with operands and result rounded to PRODUCT_ROUNDING."""
+    if PRODUCT_ROUNDING is None:
+        return X @ Y
+    t = PRODUCT_ROUNDING
+    return (np.asarray(X).astype(t) @ np.asarray(Y).astype(t)).astype(np.float64)
+
+
+# ---------------------------------------------------------------------------
 # Section 2.3, Algorithm HALS
 # ---------------------------------------------------------------------------
 
@@ -197,12 +218,12 @@ def hals_sweep(M, V, W):
     """One pass of the while-loop of Algorithm HALS: all columns of V, then all rows of W."""
     V = np.array(V, dtype=np.float64)
     W = np.array(W, dtype=np.float64)
-    A = M @ W.T
-    B = W @ W.T
+    A = product(M, W.T)
+    B = product(W, W.T)
     for k in range(V.shape[1]):
         hals_update_V_column(V, A, B, k)
-    C = V.T @ M
-    D = V.T @ V
+    C = product(V.T, M)
+    D = product(V.T, V)
     for k in range(W.shape[0]):
         hals_update_W_row(W, C, D, k)
     return V, W
@@ -219,8 +240,8 @@ def mu_sweep(M, V, W):
     """
     V = np.array(V, dtype=np.float64)
     W = np.array(W, dtype=np.float64)
-    V = V * (M @ W.T) / np.maximum(V @ (W @ W.T), EPS_MU)
-    W = W * (V.T @ M) / np.maximum((V.T @ V) @ W, EPS_MU)
+    V = V * product(M, W.T) / np.maximum(V @ product(W, W.T), EPS_MU)
+    W = W * product(V.T, M) / np.maximum(product(V.T, V) @ W, EPS_MU)
     return V, W
 
 
@@ -288,11 +309,11 @@ def anls_sweep(M, V, W):
     W = np.array(W, dtype=np.float64)
     m = M.shape[0]
     n = M.shape[1]
-    G = W @ W.T
-    A = M @ W.T
+    G = product(W, W.T)
+    A = product(M, W.T)
     V = np.stack([nnls_active_set(G, A[i]) for i in range(m)])
-    D = V.T @ V
-    C = V.T @ M
+    D = product(V.T, V)
+    C = product(V.T, M)
     W = np.stack([nnls_active_set(D, C[:, j]) for j in range(n)], axis=1)
     return V, W
 
@@ -376,17 +397,45 @@ def full_multigrid(Ms, grids, V0, W0, algo: str, L: int, K: int, level: int = 0,
     return vcycle(Ms, grids, V, W, algo, L, (3 * K) // 4, level, None, trace)
 
 
-CYCLES = {"vcycle": vcycle, "ni": nested_iteration, "fmg": full_multigrid}
+def wcycle(Ms, grids, V, W, algo: str, L: int, K: int, level: int = 0, trace=None):
+    """W-cycle, one of the other grid cycles Section 7 names as an extension.
+
+    As Algorithm V-cycle, except that the coarser level is visited twice in a row
+    before the prolongation.  READING (sweep budget, as for the V-cycle): each visit
+    gets half the coarse budget, K // 2, so the coarse share of the time matches the
+    V-cycle's; with two levels the W-cycle is the V-cycle.
+    """
+    M = Ms[level]
+    if L == 1:
+        return smooth(M, V, W, algo, K, trace, level + 1)
+    V, W = smooth(M, V, W, algo, K // 4, trace, level + 1)
+    Vc = restrict(V, *grids[level])
+    for _ in range(2):
+        Vc, W = wcycle(Ms, grids, Vc, W, algo, L - 1, K // 2, level + 1, trace)
+    V = prolong(Vc, *grids[level + 1], *grids[level])
+    return smooth(M, V, W, algo, K // 2, trace, level + 1)
+
+
+CYCLES = {"vcycle": vcycle, "ni": nested_iteration, "fmg": full_multigrid, "wcycle": wcycle}
 
 
 def solve(M, grid_h: int, grid_w: int, V0, W0, algo: str = "hals", levels: int = 1, K: int = 100,
-          cycle: str = "vcycle", trace=None):
-    """Multilevel NMF of M (m = grid_h * grid_w rows) from (V0, W0); returns (V, W)."""
+          cycle: str = "vcycle", trace=None, products: str = "fp64"):
+    """Multilevel NMF of M (m = grid_h * grid_w rows) from (V0, W0); returns (V, W).
+
+    products: "fp64" (default) or "fp32" (the four products of each sweep rounded to
+    float32, see PRODUCT_ROUNDING)."""
+    global PRODUCT_ROUNDING
     M = np.asarray(M, dtype=np.float64)
     Ms = restrict_hierarchy(M, grid_h, grid_w, levels)
     grids = grid_hierarchy(grid_h, grid_w, levels)
     V = np.asarray(V0, dtype=np.float64)
     W = np.asarray(W0, dtype=np.float64)
-    if cycle == "vcycle":
-        return vcycle(Ms, grids, V, W, algo, levels, K, trace=trace)
-    return CYCLES[cycle](Ms, grids, V, W, algo, levels, K, trace=trace)
+    saved = PRODUCT_ROUNDING
+    PRODUCT_ROUNDING = {"fp64": None, "fp32": np.float32}[products]
+    try:
+        if cycle == "vcycle":
+            return vcycle(Ms, grids, V, W, algo, levels, K, trace=trace)
+        return CYCLES[cycle](Ms, grids, V, W, algo, levels, K, trace=trace)
+    finally:
+        PRODUCT_ROUNDING = saved

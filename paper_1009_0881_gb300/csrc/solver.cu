@@ -69,6 +69,20 @@ struct ScheduleBuilder {
         ops.push_back({OP_PROLONG_V, lvl, 0});
         sweeps(lvl, (3 * K) / 4);
     }
+    // W-cycle (an extension Section 7 names): as the V-cycle, but the coarser level is
+    // visited twice in a row, each visit with half the coarse budget (K/2).
+    void wcycle(int lvl, int L, int64_t K) {
+        if (L == 1) {
+            sweeps(lvl, K);
+            return;
+        }
+        sweeps(lvl, K / 4);
+        ops.push_back({OP_RESTRICT_V, lvl, 0});
+        wcycle(lvl + 1, L - 1, K / 2);
+        wcycle(lvl + 1, L - 1, K / 2);
+        ops.push_back({OP_PROLONG_V, lvl, 0});
+        sweeps(lvl, K / 2);
+    }
     // Algorithm Full Multigrid: FMG on the coarser level (budget K), prolong,
     // then a V-cycle over the L levels with budget floor(3K/4).
     void fmg(int lvl, int L, int64_t K) {
@@ -89,6 +103,8 @@ std::vector<Op> build_schedule(nmf_cycle cyc, int L, int64_t K) {
         b.nested(0, L, K);
     else if (cyc == NMF_FMG)
         b.fmg(0, L, K);
+    else if (cyc == NMF_WCYCLE)
+        b.wcycle(0, L, K);
     else
         b.vcycle(0, L, K);
     return b.ops;
@@ -1133,7 +1149,8 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     if (K < 0) return fail(h, NMF_EINVAL, "iters must be >= 0");
     if (algo != NMF_HALS && algo != NMF_MU && algo != NMF_ANLS) return fail(h, NMF_EINVAL, "unknown algorithm");
     const nmf_cycle cyc = opt ? opt->cycle : NMF_VCYCLE;
-    if (cyc != NMF_VCYCLE && cyc != NMF_NESTED && cyc != NMF_FMG) return fail(h, NMF_EINVAL, "unknown cycle");
+    if (cyc != NMF_VCYCLE && cyc != NMF_NESTED && cyc != NMF_FMG && cyc != NMF_WCYCLE)
+        return fail(h, NMF_EINVAL, "unknown cycle");
     const int64_t stop_after = opt ? opt->stop_after : 0;
     const bool trace = opt && opt->trace && opt->trace_len > 0;
     CK(cudaSetDevice(h->device));
@@ -1240,7 +1257,7 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
         if (q.levels < 1 || q.levels > 16 || q.iters < 0) return fail(h, NMF_EINVAL, "problem %d: bad levels/iters", i);
         if (q.algo != NMF_HALS && q.algo != NMF_MU && q.algo != NMF_ANLS)
             return fail(h, NMF_EINVAL, "problem %d: unknown algorithm", i);
-        if (q.cycle != NMF_VCYCLE && q.cycle != NMF_NESTED && q.cycle != NMF_FMG)
+        if (q.cycle != NMF_VCYCLE && q.cycle != NMF_NESTED && q.cycle != NMF_FMG && q.cycle != NMF_WCYCLE)
             return fail(h, NMF_EINVAL, "problem %d: unknown cycle", i);
     }
     CK(cudaSetDevice(h->device));
@@ -1434,7 +1451,7 @@ const char* nmf_last_error(nmf_handle h) {
 
 int64_t nmf_schedule(nmf_cycle cycle, int levels, int iters, int64_t* sweeps_per_level) {
     if (levels < 1 || levels > 16 || iters < 0) return NMF_EINVAL;
-    if (cycle != NMF_VCYCLE && cycle != NMF_NESTED && cycle != NMF_FMG) return NMF_EINVAL;
+    if (cycle != NMF_VCYCLE && cycle != NMF_NESTED && cycle != NMF_FMG && cycle != NMF_WCYCLE) return NMF_EINVAL;
     std::vector<Op> ops = build_schedule(cycle, levels, iters);
     int64_t total = 0;
     if (sweeps_per_level)

@@ -16,10 +16,10 @@ from . import build as _build
 
 NMF_HALS, NMF_MU, NMF_ANLS = 0, 1, 2
 NMF_FP32, NMF_BF16 = 0, 1
-NMF_VCYCLE, NMF_NESTED, NMF_FMG = 0, 1, 2
+NMF_VCYCLE, NMF_NESTED, NMF_FMG, NMF_WCYCLE = 0, 1, 2, 3
 NMF_OK, NMF_EINVAL, NMF_ENOMEM, NMF_ENOCONV, NMF_ECUDA, NMF_ETIMEOUT, NMF_EBUSY, NMF_ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 ALGOS = {"hals": NMF_HALS, "mu": NMF_MU, "anls": NMF_ANLS}
-CYCLES = {"vcycle": NMF_VCYCLE, "ni": NMF_NESTED, "fmg": NMF_FMG}
+CYCLES = {"vcycle": NMF_VCYCLE, "ni": NMF_NESTED, "fmg": NMF_FMG, "wcycle": NMF_WCYCLE}
 
 STATUS = {0: "NMF_OK", -1: "NMF_EINVAL", -2: "NMF_ENOMEM", -3: "NMF_ENOCONV", -4: "NMF_ECUDA",
           -5: "NMF_ETIMEOUT", -6: "NMF_EBUSY", -7: "NMF_ETOOBIG"}

@@ -34,6 +34,9 @@ CASES = [
     ("grid19_hals_ni_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "ni"),
     ("grid19_mu_fmg_L3_K100", "grid19_n2429_r49", "mu", 3, 100, "fmg"),
     ("grid19_anls_fmg_L3_K8", "grid19_n2429_r49", "anls", 3, 8, "fmg"),
+    # W-cycle (Section 7 extension)
+    ("grid19_hals_wcycle_L3_K100", "grid19_n2429_r49", "hals", 3, 100, "wcycle"),
+    ("grid16_mu_wcycle_L3_K100", "grid16_n1000_r10", "mu", 3, 100, "wcycle"),
     # full multigrid and nested iteration start on the coarsest level: keep m_l >= r there
     ("grid19_hals_fmg_L2_K100", "grid19_n2429_r49", "hals", 2, 100, "fmg"),
     ("grid19_hals_ni_L2_K100", "grid19_n2429_r49", "hals", 2, 100, "ni"),
@@ -45,6 +48,13 @@ CASES = [
     ("grid256_hals_L3_K20", "grid256_n2000_r64", "hals", 3, 20, "vcycle"),
     ("grid256_hals_L3_K100", "grid256_n2000_r64", "hals", 3, 100, "vcycle"),
 ]
+
+
+# Cycles that start on a level with fewer pixels than the rank: their result depends on the
+# rounding of the products (oracle reading PRODUCT_ROUNDING), so the float32-product value is
+# stored beside the FP64 one.
+FP32_PRODUCT_CASES = {"grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100", "grid19_mu_fmg_L3_K100",
+                      "grid19_anls_fmg_L3_K8"}
 
 
 def _store(path, name, entry):
@@ -69,8 +79,12 @@ def main(only=None):
         t = time.time()
         V, W = o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc)
         f = o.objective(p.M.astype(np.float64), V, W)
-        _store(path, name, {"workload": wl, "algo": algo, "levels": L, "K": K, "cycle": cyc, "objective": f,
-                            "norm_M": float(np.linalg.norm(p.M.astype(np.float64)))})
+        entry = {"workload": wl, "algo": algo, "levels": L, "K": K, "cycle": cyc, "objective": f,
+                 "norm_M": float(np.linalg.norm(p.M.astype(np.float64)))}
+        if name in FP32_PRODUCT_CASES:
+            V, W = o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc, products="fp32")
+            entry["objective_fp32_products"] = o.objective(p.M.astype(np.float64), V, W)
+        _store(path, name, entry)
         print(f"{name}: {f:.10g} ({time.time() - t:.1f} s)", flush=True)
 
 

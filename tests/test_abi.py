@@ -47,7 +47,7 @@ def test_exports_via_nm(lib):
         assert re.search(rf"\bT {name}$", out, flags=re.M), name
 
 
-@pytest.mark.parametrize("cycle", ["vcycle", "ni", "fmg"])
+@pytest.mark.parametrize("cycle", ["vcycle", "ni", "fmg", "wcycle"])
 @pytest.mark.parametrize("L,K", [(1, 10), (2, 100), (3, 100), (3, 500), (4, 37), (5, 8)])
 def test_schedule_matches_oracle(lib, cycle, L, K):
     # the library's cycle schedule is integer host logic: bit-exact with the oracle's recursion

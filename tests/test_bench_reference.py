@@ -29,6 +29,13 @@ def test_reference_arm_prints_one_contract_line():
     assert d["unit"] == "sweeps/s" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["n_gpus"] == 1
     assert d["config"]["workload"].startswith("grid19_n2429_r49")
+    # the config describes the sample each step actually times: its sweep count is the one
+    # the step ran, and ms_per_step divided by it is the time per sweep
+    import bench
+    assert d["config"]["iters"] == bench.REFERENCE_ITERS
+    assert d["config"]["sweeps_per_step"] == sum(bench._schedule_py(d["config"]["levels"], bench.REFERENCE_ITERS))
+    assert abs(d["value"] - d["config"]["sweeps_per_step"] / (d["ms_per_step"] / 1e3)) <= 1e-6 * d["value"]
+    assert "l2" not in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e2e = d["e2e"]

@@ -223,12 +223,29 @@ def test_cycle_final_objective_matches_oracle(h, name):
 # (1e-3 relative, as for every cycle), and the coarse-level ANLS results are checked for
 # the optimality conditions below instead.
 HEADLINE_L3 = ["grid19_anls_L3_K8", "grid19_anls_L3_K500", "grid19_anls_L1_K500", "grid19_anls_fmg_L3_K8",
-               "grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100", "grid19_mu_fmg_L3_K100"]
+               "grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100", "grid19_mu_fmg_L3_K100",
+               "grid19_hals_wcycle_L3_K100", "grid16_mu_wcycle_L3_K100"]
 
 
 @pytest.mark.parametrize("name", HEADLINE_L3)
 def test_headline_cycles_at_three_levels_match_oracle(h, name):
-    test_cycle_final_objective_matches_oracle(h, name)
+    g = GOLDEN[name]
+    if "objective_fp32_products" not in g:
+        test_cycle_final_objective_matches_oracle(h, name)
+        return
+    # NI and FMG begin with K sweeps on the 5 x 5 level (25 pixels < r = 49), where the
+    # objective is flat and the point the sweeps settle on depends on how the products
+    # are rounded: the FP64 oracle itself moves by more than 1e-3 when only its four
+    # products are rounded to float32.  The GPU (float32 products) is compared at 1e-3
+    # with that oracle run; the FP64 value is kept beside it.
+    gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    V, W = p.V.copy(), p.W.copy()
+    h.solve(p.M, gh, gw, V, W, g["algo"], levels=g["levels"], iters=g["K"], cycle=g["cycle"])
+    f = o.objective(p.M, V, W)
+    f32 = g["objective_fp32_products"]
+    assert abs(f - f32) <= 1e-3 * f32, (f, f32, g["objective"])
+    print(f"{name}: GPU {f:.6g}, oracle float32 products {f32:.6g}, oracle FP64 {g['objective']:.6g}")
 
 
 def _kkt_violation(G, B, X):

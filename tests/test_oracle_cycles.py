@@ -183,3 +183,40 @@ def test_fmg_data_flow(algo):
     np.testing.assert_array_equal(hooks[1][3], W1)
     np.testing.assert_array_equal(V, Vf)
     np.testing.assert_array_equal(W, Wf)
+
+
+def test_wcycle_with_two_levels_is_the_vcycle():
+    # two visits of K/2 coarse sweeps in a row are one run of K sweeps (even K)
+    p = synth.make_problem(9, 9, 30, 4, data_seed=12)
+    for algo in ("hals", "mu"):
+        a = o.solve(p.M, 9, 9, p.V, p.W, algo, levels=2, K=8, cycle="wcycle")
+        b = o.solve(p.M, 9, 9, p.V, p.W, algo, levels=2, K=8, cycle="vcycle")
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_wcycle_order_visits_the_coarser_level_twice():
+    K = 8
+    one = [2] * (K // 8) + [3] * (K // 4) * 2 + [2] * (K // 4)   # a visit of level 2 with budget K/2
+    assert _level_sequence("wcycle", 3, K) == [1] * (K // 4) + one + one + [1] * (K // 2)
+
+
+def test_wcycle_data_flow():
+    # rebuilt from the pinned pieces: pre-smoothing, restriction, two coarse W-cycles with
+    # budget K/2 that pass V and W on to each other, prolongation, post-smoothing
+    Ms, grids, V0, W0 = _bottom_up_problem()
+    K = 8
+    V, W = o.wcycle(Ms, grids, V0, W0, "hals", 3, K)
+    Vp, Wp = o.smooth(Ms[0], V0, W0, "hals", K // 4)
+    Vc = o.restrict(Vp, *grids[0])
+    Wc = Wp
+    for _ in range(2):
+        # a level-2 visit with budget K/2: its own two level-3 visits with budget K/4
+        Va, Wa = o.smooth(Ms[1], Vc, Wc, "hals", (K // 2) // 4)
+        Vcc = o.restrict(Va, *grids[1])
+        Vcc, Wa = o.smooth(Ms[2], Vcc, Wa, "hals", 2 * ((K // 2) // 2))
+        Va = o.prolong(Vcc, *grids[2], *grids[1])
+        Vc, Wc = o.smooth(Ms[1], Va, Wa, "hals", (K // 2) // 2)
+    Vf, Wf = o.smooth(Ms[0], o.prolong(Vc, *grids[1], *grids[0]), Wc, "hals", K // 2)
+    np.testing.assert_array_equal(V, Vf)
+    np.testing.assert_array_equal(W, Wf)

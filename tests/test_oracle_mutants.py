@@ -152,6 +152,18 @@ def _fmg_coarse_w0(Ms, grids, V0, W0, algo, L, K, level=0, trace=None, hooks=Non
     return o.vcycle(Ms, grids, V, W0, algo, L, (3 * K) // 4, level, None, trace)
 
 
+def _wcycle_single_visit(Ms, grids, V, W, algo, L, K, level=0, trace=None):
+    # the coarser level visited once (a V-cycle with half the coarse budget)
+    M = Ms[level]
+    if L == 1:
+        return o.smooth(M, V, W, algo, K, trace, level + 1)
+    V, W = o.smooth(M, V, W, algo, K // 4, trace, level + 1)
+    Vc = o.restrict(V, *grids[level])
+    Vc, W = _wcycle_single_visit(Ms, grids, Vc, W, algo, L - 1, K // 2, level + 1, trace)
+    V = o.prolong(Vc, *grids[level + 1], *grids[level])
+    return o.smooth(M, V, W, algo, K // 2, trace, level + 1)
+
+
 def _table1_checks():
     return [lambda row=row: tc.test_vcycle_sweep_allocation_matches_table1(row) for row in tc._table1_rows()]
 
@@ -184,6 +196,9 @@ MUTANTS = {
                                [lambda: tc.test_nested_iteration_data_flow("hals")]),
     "FMG V-cycle from V0": ("full_multigrid", _fmg_vcycle_from_v0, [lambda: tc.test_fmg_data_flow("hals")]),
     "FMG V-cycle with the initial W": ("full_multigrid", _fmg_coarse_w0, [lambda: tc.test_fmg_data_flow("hals")]),
+    "W-cycle visits the coarser level once": ("wcycle", _wcycle_single_visit,
+                                              [tc.test_wcycle_order_visits_the_coarser_level_twice,
+                                               tc.test_wcycle_data_flow]),
 }
 
 
@@ -191,6 +206,8 @@ MUTANTS = {
 def test_pins_catch_planted_mistake(name, monkeypatch):
     attr, bad, checks = MUTANTS[name]
     monkeypatch.setattr(o, attr, bad)
+    if attr == "wcycle":
+        monkeypatch.setitem(o.CYCLES, "wcycle", bad)
     if attr == "mu_sweep":
         monkeypatch.setitem(o.SWEEPS, "mu", bad)
     assert _fails(*checks), f"no pin noticed: {name}"

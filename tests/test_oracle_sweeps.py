@@ -297,3 +297,42 @@ def test_anls_sweep_is_blockwise_optimal_and_ignores_v():
     assert (gV >= -1e-9 * s).all() and np.abs(V1 * gV).max() < 1e-9 * s
     assert (gW >= -1e-9 * s).all() and np.abs(W1 * gW).max() < 1e-9 * s
     assert o.objective(M, V1, W1) <= o.objective(M, V, W)
+
+
+def test_float32_products_exact_on_small_integers():
+    # products of small integers are exact in float32, so the rounded variant equals FP64
+    rng = np.random.default_rng(21)
+    X = rng.integers(0, 9, (7, 30)).astype(np.float64)
+    Y = rng.integers(0, 9, (30, 5)).astype(np.float64)
+    saved = o.PRODUCT_ROUNDING
+    try:
+        o.PRODUCT_ROUNDING = np.float32
+        np.testing.assert_array_equal(o.product(X, Y), X @ Y)
+    finally:
+        o.PRODUCT_ROUNDING = saved
+
+
+def test_float32_products_within_rounding_bound():
+    # |fl32(X Y) - X Y| <= (K + 2) u |X| |Y| entrywise (operand rounding plus a K-term sum),
+    # and the rounding does change the result
+    rng = np.random.default_rng(22)
+    X, Y = rng.random((20, 300)), rng.random((300, 9))
+    saved = o.PRODUCT_ROUNDING
+    try:
+        o.PRODUCT_ROUNDING = np.float32
+        P = o.product(X, Y)
+    finally:
+        o.PRODUCT_ROUNDING = saved
+    exact = X @ Y
+    u = 2.0 ** -24
+    assert np.all(np.abs(P - exact) <= (300 + 2) * u * (np.abs(X) @ np.abs(Y)))
+    assert np.any(P != exact)
+    assert o.PRODUCT_ROUNDING is None
+
+
+def test_solve_products_option_restores_fp64():
+    p = synth.make_problem(8, 8, 20, 3, data_seed=2)
+    a = o.solve(p.M, 8, 8, p.V, p.W, "hals", levels=2, K=4, products="fp32")
+    assert o.PRODUCT_ROUNDING is None
+    b = o.solve(p.M, 8, 8, p.V, p.W, "hals", levels=2, K=4)
+    assert not np.array_equal(a[0], b[0])
