@@ -123,3 +123,39 @@ def test_bad_request_fails_alone(ref):
             srv.submit(bad)
         got = _serve(srv, reqs)
     assert all(g[0] == 0 for g in got)
+
+
+def _sample_problem(row):
+    p = synth.make_problem(row["side"], row["side"], row["n"], row["r"], row["sigma"], row["index"])
+    return p, dict(M=p.M, grid_h=row["side"], grid_w=row["side"], V=p.V.copy(), W=p.W.copy(), algo=row["algo"],
+                   levels=row["levels"], iters=row["iters"])
+
+
+def test_served_sample_against_fp64_oracle(ref):
+    # a seeded, size-stratified sample of 64 requests of the serving workload (every size of the
+    # uneven pool, HALS / MU / ANLS in turn, three levels, short fixed budgets), all in flight in
+    # one server at once; each result against the FP64 oracle's objective for the same request
+    # (tests/golden/served_sample.json, written by tests/golden/make_served_sample.py).  Float32
+    # within 1e-3; BF16 operands within the BF16 floor of 2e-2 (measured on these inputs).
+    import json
+    import os
+    from conftest import ROOT
+    G = json.load(open(os.path.join(ROOT, "tests", "golden", "served_sample.json")))
+    assert len(G["requests"]) >= 64
+    bar = 1e-3 if ref.precision == native.NMF_FP32 else 2e-2
+    errs = []
+    with native.Server(0, hbm_budget_bytes=40 * 10**9, slots=8, precision=ref.precision) as srv:
+        pending = []
+        for row in G["requests"]:
+            p, d = _sample_problem(row)
+            pending.append((srv.submit(d), d, row))
+        for t, d, row in pending:
+            st, sweeps, obj, lat = srv.poll(t, -1)
+            assert st == 0, (row, st)
+            errs.append((abs(obj - row["objective"]) / row["objective"], row["algo"], row["side"], row["r"]))
+            assert (d["V"] >= 0).all() and (d["W"] >= 0).all()
+    worst = max(errs)
+    print(f"served sample ({'fp32' if ref.precision == native.NMF_FP32 else 'bf16'}): "
+          f"max rel. error {worst[0]:.2e} ({worst[1]}, side {worst[2]}, r {worst[3]}), "
+          f"median {float(np.median([e[0] for e in errs])):.2e}")
+    assert worst[0] <= bar, worst
