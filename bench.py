@@ -52,6 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-precision-form", action="store_true")
     ap.add_argument("--no-batched-form", action="store_true")
     ap.add_argument("--no-serving-form", action="store_true")
+    ap.add_argument("--no-time-to-target-table", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-rate-low", type=float, default=40.0)
@@ -460,8 +461,12 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
     out["roofline"], out["kernel_times_per_step_ms"] = roofline(args, h, Md, gh, gw, n, r, sched)
     if args.workload == WORKLOAD:
         out["other_algorithms"] = other_algorithms(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw)
+        if not args.no_time_to_target_table:
+            out["time_to_target_table"] = time_to_target_table(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw)
     if not args.no_precision_form:
         out["precision_form"] = precision_form(args)
+    if not args.no_batched_form:
+        out["oracle_sample_forms"] = oracle_sample_forms(_sample_pool())
     if not (args.no_batched_form and args.no_serving_form):
         pool = batched_problems(BATCH_COUNT)
         if not args.no_batched_form:
@@ -496,6 +501,68 @@ def _traffic(kernel):
     return t["bytes"] if hsh.hexdigest()[:16] == t["src"] else None
 
 
+def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, reps=3, warm=1):
+    """Wall time of a V-cycle solve (device-resident inputs, CUDA events) until the finest-level
+    objective first reaches (1 + 1e-3) f*, f* the FP64 oracle's final objective for the same
+    (algo, L, K): the per-sweep trace locates that sweep, then solves stopped right after it
+    are timed.  None if the schedule never reaches the target."""
+    import numpy as np
+    import torch
+
+    from paper_1009_0881_gb300 import native
+
+    sched = native.schedule("vcycle", L, K)
+    target = (1 + 1e-3) * fstar
+    Vd.copy_(V0d)
+    Wd.copy_(W0d)
+    tr = h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, trace_len=sched[0])
+    hit = np.nonzero(tr <= target)[0]
+    res = {"algo": algo, "levels": L, "iters": K, "oracle_fp64": fstar, "objective_target": target,
+           "final_objective_gpu": float(tr[-1]) if len(tr) else None}
+    if not len(hit):
+        res["ms"] = None
+        return res
+    s_fine = int(hit[0]) + 1
+    pre = K // 4 if L > 1 else K
+    stop = s_fine if s_fine <= pre else s_fine + sum(sched[1:])
+    ms = []
+    for it in range(warm + reps):
+        Vd.copy_(V0d)
+        Wd.copy_(W0d)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, stop_after=stop)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= warm:
+            ms.append(e0.elapsed_time(e1))
+    f = h.error(Md, Vd, Wd)
+    res.update(ms=statistics.median(ms), sweeps=stop, fine_sweeps=s_fine, objective_at_stop=f,
+               reached=bool(f <= target * (1 + 1e-12)))
+    return res
+
+
+def time_to_target_table(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw):
+    """Time to (1 + 1e-3) f* for HALS, MU and ANLS (active set and block pivoting), multilevel
+    (L = 3) and single-level (L = 1), K = 500, on the 19 x 19 workload; f* is the FP64
+    oracle's objective of each (algo, L).  ANLS with block pivoting uses the active-set
+    oracle's f* (the two reach the same NNLS solutions)."""
+    out = {}
+    for algo in ("hals", "mu", "anls", "anls_bpp"):
+        for L in (3, 1):
+            key = f"grid19_{'anls' if algo == 'anls_bpp' else algo}_L{L}_K{args.iters}"
+            fstar = golden.get(key, {}).get("objective")
+            name = f"{algo}_L{L}"
+            if fstar is None:
+                out[name] = {"ms": None, "note": f"no FP64 oracle value stored for {key}"}
+                continue
+            slow = algo.startswith("anls")
+            out[name] = time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, args.iters, fstar,
+                                       reps=1 if slow else 3, warm=0 if slow else 1)
+    return out
+
+
 def other_algorithms(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw):
     """MU and ANLS on the same workload, multilevel (L = 3) next to single-level, same sweep
     budget; objective against the FP64 oracle's stored value where one exists."""
@@ -504,7 +571,7 @@ def other_algorithms(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw):
     from paper_1009_0881_gb300 import native
 
     out = {}
-    for algo in ("mu", "anls"):
+    for algo in ("mu", "anls", "anls_bpp"):
         for L in (3, 1):
             sweeps = sum(native.schedule("vcycle", L, args.iters))
             ms = []
@@ -520,7 +587,7 @@ def other_algorithms(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw):
                 if it:
                     ms.append(e0.elapsed_time(e1))
             f = h.error(Md, Vd, Wd)
-            fstar = golden.get(f"grid19_{algo}_L{L}_K{args.iters}", {}).get("objective")
+            fstar = golden.get(f"grid19_{'anls' if algo == 'anls_bpp' else algo}_L{L}_K{args.iters}", {}).get("objective")
             out[f"{algo}_L{L}"] = {"ms_per_solve": ms[0], "sweeps": sweeps, "sweeps_per_s": sweeps / (ms[0] / 1e3),
                                    "objective": f, "oracle_fp64": fstar,
                                    "rel_diff": None if fstar is None else abs(f - fstar) / fstar}
@@ -540,12 +607,10 @@ def roofline(args, h, Md, gh, gw, n, r, sched):
     The FP32 path runs one fused kernel per half-sweep (products, reduction and
     factor update) and, on coarse levels whose V has at most 32 rows, all sweeps of
     a run in one persistent kernel.  Algorithmic flops per sweep (Appendix A.1
-    accounting, multiply-add = 2):
-      V-step  A = M W^T (2 m_l n r) + V(W W^T) (2 m_l r^2)
-      W-step  C = V^T M (2 m_l n r) + (V^T V) W (2 n r^2)
-    The Gram matrices W W^T and V^T V (2 n r^2, 2 m_l r^2) are also formed, from
-    the updated rows, but are counted once with the update term as in Appendix A.1.
-    The roofline line reports the kernel with the larger share of the step.
+    accounting, multiply-add = 2): F_l = 4 m_l n r + 4 (m_l + n) r^2, i.e. the two
+    products with M plus the Gram matrices W W^T, V^T V and the update terms
+    V (W W^T), (V^T V) W.  The roofline line reports the kernel with the larger
+    share of the step.
     """
     import torch
 
@@ -565,8 +630,10 @@ def roofline(args, h, Md, gh, gw, n, r, sched):
     for lvl, count in enumerate(sched):
         ml = hh * ww
         V = torch.rand(ml, r, generator=g).to(dev)
-        flv = 2 * ml * n * r + 2 * ml * r * r
-        flw = 2 * ml * n * r + 2 * n * r * r
+        # Appendix A.1 accounting of one sweep (multiply-add = 2): 4 m_l n r for the two
+        # products with M, 4 (m_l + n) r^2 for the Gram matrices and the r^2 update terms
+        flv = 2 * ml * n * r + 2 * (ml + n) * r * r
+        flw = 2 * ml * n * r + 2 * (ml + n) * r * r
         tc = h.profile_coarse(Ml, V, W, args.algo, sweeps=100) if lvl > 0 else None
         if tc is not None:
             kinds[cr][0] += count * tc
@@ -625,7 +692,8 @@ def precision_form(args, reps=3):
         key = f"{wl.split('_')[0]}_hals_L{L}_K{K}"
         fstar = golden.get(key, {}).get("objective")
         res = {"levels": L, "iters": K, "sweeps": sweeps, "m": m, "n": n, "r": r}
-        for label, prec in (("bf16_tcgen05", native.NMF_BF16), ("fp32", native.NMF_FP32)):
+        for label, prec in (("bf16_tcgen05", native.NMF_BF16), ("bf16_fp32_finish", native.NMF_BF16_FP32),
+                            ("fp32", native.NMF_FP32)):
             with native.Handle(0, precision=prec) as hh:
                 hh.set_stream(stream.cuda_stream)
                 V = V0.clone()
@@ -646,6 +714,15 @@ def precision_form(args, reps=3):
                 t = statistics.median(ms)
                 entry = {"ms_per_solve": t, "sweeps_per_s": sweeps / (t / 1e3), "objective": f,
                          "rel_diff_vs_fp64_oracle": None if fstar is None else (f - fstar) / fstar}
+                if fstar is not None:
+                    # time to (1 + 1e-3) f*: the float32 path from its trace; the BF16 forms
+                    # reach it only at the end of the solve if at all (their last sweeps decide)
+                    if prec == native.NMF_FP32:
+                        Vt, Wt = V0.clone(), W0.clone()
+                        tt = time_to_target(hh, Md, V0, W0, Vt, Wt, stream, gh, gw, "hals", L, K, fstar)
+                        entry["time_to_1e-3_ms"] = tt["ms"]
+                    else:
+                        entry["time_to_1e-3_ms"] = t if f <= (1 + 1e-3) * fstar else None
                 if prec == native.NMF_BF16:
                     # tcgen05 product of the V-step at the finest level: HBM roofline
                     g = torch.Generator(device="cpu").manual_seed(1)
@@ -656,12 +733,19 @@ def precision_form(args, reps=3):
                     ach = bytes_v / (tt[0] / 1e3) / 1e9
                     entry["kernel_ms"] = {"tc_gemm V-step": tt[0], "gram+rows V": tt[1], "tc_gemm W-step": tt[2],
                                           "gram+rows W": tt[3]}
+                    # DRAM traffic was captured on the 256 x 256 workload only
+                    captured = wl == "grid256_n2000_r64"
                     entry["roofline"] = {"kernel": "tc_gemm_kernel (V-step, A = M W^T, finest level)",
                                          "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                                         "frac": ach / hbm, "traffic": _traffic("tc_gemm_kernel"),
+                                         "frac": ach / hbm, "peak_basis": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                                         "traffic": _traffic("tc_gemm_kernel") if captured else None,
+                                         "traffic_scope": TRAFFIC["tc_gemm_kernel"]["scope"] if captured
+                                         else "not captured on this workload",
                                          "algorithmic_bytes": bytes_v}
                 res[label] = entry
         res["oracle_fp64_objective"] = fstar
+        a, b = res["bf16_fp32_finish"].get("time_to_1e-3_ms"), res["fp32"].get("time_to_1e-3_ms")
+        res["bf16_fp32_finish_speedup_to_1e-3"] = (b / a) if (a and b) else None
         out[wl] = res
     return out
 
@@ -672,8 +756,9 @@ def precision_form(args, reps=3):
 BATCH_COUNT = 64
 BATCH_LEVELS = 3
 BATCH_ITERS = {"hals": 200, "mu": 200, "anls": 20}
-# serving: per-request sweep budgets (ANLS sweeps are exact block minimisations, far costlier)
-SERVE_ITERS = {"hals": 100, "mu": 100, "anls": 8}
+# serving: per-request sweep caps (the 1e-3 relative-change rule ends most requests earlier;
+# ANLS sweeps are exact block minimisations, far costlier, and converge in few sweeps)
+SERVE_ITERS = {"hals": 100, "mu": 100, "anls": 40}
 BATCH_TOL = 1e-3
 
 
@@ -752,6 +837,74 @@ def batched_form(args, pool, reps=3):
     return out
 
 
+def _sample_pool():
+    """The 64 requests of tests/golden/served_sample.json with their FP64 oracle objectives."""
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+
+    from paper_1009_0881_gb300 import synth
+
+    G = json.load(open(os.path.join(ROOT, "tests", "golden", "served_sample.json")))
+    rows = G["requests"]
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(synth.make_problem, q["side"], q["side"], q["n"], q["r"], q["sigma"], q["index"])
+                for q in rows]
+        return [(q, f.result()) for q, f in zip(rows, futs)]
+
+
+def oracle_sample_forms(sample, reps=3):
+    """The 64 sampled requests (uneven sizes, HALS / MU / ANLS, three levels, short fixed
+    budgets) solved as one batch and through the server, in each precision, every result
+    against the FP64 oracle's objective for the same request: time per batch, solves/s and
+    the relative errors (the precision forms' time to results within 1e-3 of the oracle)."""
+    import numpy as np
+    import torch
+
+    from paper_1009_0881_gb300 import native
+
+    stream = torch.cuda.current_stream()
+    Mds = [torch.from_numpy(p.M).cuda() for _, p in sample]
+    out = {"requests": len(sample), "source": "tests/golden/served_sample.json (FP64 oracle objectives)"}
+    for label, prec in (("fp32", native.NMF_FP32), ("bf16", native.NMF_BF16), ("bf16_fp32_finish", native.NMF_BF16_FP32)):
+        def reqs():
+            return [dict(M=Md, grid_h=q["side"], grid_w=q["side"], V=p.V.copy(), W=p.W.copy(), algo=q["algo"],
+                         levels=q["levels"], iters=q["iters"]) for (q, p), Md in zip(sample, Mds)]
+        res = {}
+        with native.Handle(0, precision=prec) as hh:
+            hh.set_stream(stream.cuda_stream)
+            ms = []
+            for it in range(1 + reps):
+                batch = reqs()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                got = hh.solve_batch(batch)
+                e1.record(stream)
+                e1.synchronize()
+                if it:
+                    ms.append(e0.elapsed_time(e1))
+            errs = [abs(g[2] - q["objective"]) / q["objective"] for g, (q, _) in zip(got, sample)]
+            res["batch"] = {"ms_per_batch": statistics.median(ms), "solves_per_s": len(sample) / (statistics.median(ms) / 1e3),
+                            "max_rel_error": max(errs), "median_rel_error": float(np.median(errs)),
+                            "within_1e-3": int(sum(e <= 1e-3 for e in errs))}
+        with native.Server(0, hbm_budget_bytes=40 * 10**9, slots=8, precision=prec) as srv:
+            t0 = time.perf_counter()
+            tickets = [srv.submit(d) for d in reqs()]
+            got = [srv.poll(t, -1) for t in tickets]
+            wall = time.perf_counter() - t0
+            errs = [abs(g[2] - q["objective"]) / q["objective"] for g, (q, _) in zip(got, sample)]
+            lat = np.array([g[3] for g in got])
+            res["served"] = {"wall_s": wall, "max_rel_error": max(errs), "median_rel_error": float(np.median(errs)),
+                             "within_1e-3": int(sum(e <= 1e-3 for e in errs)),
+                             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                             "note": "all 64 submitted at once, first-seen shapes (plans and graphs built inside)"}
+        out[label] = res
+    del Mds
+    torch.cuda.empty_cache()
+    return out
+
+
 def serving_form(args, pool):
     """Poisson arrivals into nmf_server: sizes from the 64-problem pool, algorithm uniform over
     HALS/MU/ANLS, 40 GB workspace budget.  M stays on the device; each request brings its
@@ -761,25 +914,32 @@ def serving_form(args, pool):
 
     from paper_1009_0881_gb300 import native
 
-    Mds = [torch.from_numpy(p.M).cuda() for p in pool]
-    torch.cuda.synchronize()
+    # each request brings M from pinned host memory: its upload is part of its latency
+    Mhs = [torch.from_numpy(p.M).pin_memory() for p in pool]
     algos = ("hals", "mu", "anls")
     budget = 40 * 10**9
     out = {"rate_per_s": args.serve_rate, "low_rate_per_s": args.serve_rate_low, "seconds": args.serve_seconds,
            "slots": args.serve_slots, "hbm_budget_bytes": budget, "levels": BATCH_LEVELS, "iters_cap": SERVE_ITERS,
            "rel_tol": BATCH_TOL, "sizes": "uniform over the 64 seeded batched-form problems",
-           "latency": "from nmf_server_submit to completion"}
-    for label, prec in (("fp32", native.NMF_FP32), ("bf16", native.NMF_BF16)):
-        with native.Server(0, hbm_budget_bytes=budget, slots=args.serve_slots, precision=prec) as srv:
-            # warm-up: every (problem, algorithm) once, so the slots' graphs and workspaces exist
-            t0 = time.perf_counter()
-            tickets = [srv.submit(_request(p, Md, a, iters=SERVE_ITERS)) for p, Md in zip(pool, Mds) for a in algos]
-            warm = [srv.poll(t, -1) for t in tickets]
-            res = {"warmup_s": time.perf_counter() - t0, "warmup_ok": all(w[0] == 0 for w in warm)}
-            res["offered"] = _poisson_run(srv, pool, Mds, args.serve_rate, args.serve_seconds, seed=7)
-            res["low_rate"] = _poisson_run(srv, pool, Mds, args.serve_rate_low, args.serve_seconds, seed=8)
-            out[label] = res
-    del Mds
+           "latency": "from nmf_server_submit to completion; M, V0, W0 uploaded from pinned host memory "
+                      "and V, W returned to it inside that time",
+           "max_batch": "requests a slot takes at once (NMF_SERVE_MAX_BATCH): 16 = one graph per combination "
+                        "of shapes, 1 = the cached graph of each shape"}
+    for label, prec in (("fp32", native.NMF_FP32), ("bf16", native.NMF_BF16), ("bf16_fp32_finish", native.NMF_BF16_FP32)):
+        for mb in (16, 1):
+            os.environ["NMF_SERVE_MAX_BATCH"] = str(mb)
+            with native.Server(0, hbm_budget_bytes=budget, slots=args.serve_slots, precision=prec) as srv:
+                # warm-up: every (problem, algorithm) once, so the slots' graphs and workspaces exist
+                t0 = time.perf_counter()
+                tickets = [srv.submit(_request(p, Mh, a, iters=SERVE_ITERS)) for p, Mh in zip(pool, Mhs) for a in algos]
+                warm = [srv.poll(t, -1) for t in tickets]
+                res = {"warmup_s": time.perf_counter() - t0, "warmup_ok": all(w[0] == 0 for w in warm)}
+                res["offered"] = _poisson_run(srv, pool, Mhs, args.serve_rate, args.serve_seconds, seed=7)
+                if mb == 16:
+                    res["low_rate"] = _poisson_run(srv, pool, Mhs, args.serve_rate_low, args.serve_seconds, seed=8)
+                out[f"{label}_max_batch{mb}"] = res
+    os.environ.pop("NMF_SERVE_MAX_BATCH", None)
+    del Mhs
     torch.cuda.empty_cache()
     return out
 

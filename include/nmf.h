@@ -42,13 +42,22 @@ typedef struct nmf_ctx* nmf_handle;
 typedef enum {
     NMF_HALS = 0, /* Algorithm HALS (Section 2.3): r exact column updates of V, then r row updates of W */
     NMF_MU = 1,   /* Algorithm MU (Section 2.2): Lee-Seung multiplicative updates */
-    NMF_ANLS = 2  /* Algorithm ANLS (Section 2.1, Appendix A.2): exact NNLS for V then W (FP64 active set) */
+    NMF_ANLS = 2, /* Algorithm ANLS (Section 2.1, Appendix A.2): exact NNLS for V then W (FP64 active set) */
+    NMF_ANLS_BPP = 3 /* Algorithm ANLS with its NNLS problems solved by block principal pivoting (the
+                        alternative the ANLS footnote of Section 2.1 names), FP64; rows where a passive
+                        block is numerically singular, or where pivoting does not finish within 5r
+                        exchanges, are solved by the active-set method instead */
 } nmf_algo;
 
 /* Storage precision of M and of the GEMM operands. */
 typedef enum {
-    NMF_FP32 = 0, /* everything float32 */
-    NMF_BF16 = 1  /* M, V, W as bfloat16 GEMM operands, float32 accumulation and updates */
+    NMF_FP32 = 0,     /* everything float32 */
+    NMF_BF16 = 1,     /* M, V, W as bfloat16 GEMM operands, float32 accumulation and updates */
+    NMF_BF16_FP32 = 2 /* NMF_BF16 for every sweep except the last quarter (at least one sweep) of the
+                         last run of finest-level sweeps, which runs the float32 kernels on the
+                         float32 M: the BF16 sweeps do most of the descent, the float32 ones remove
+                         the bias that BF16 rounding of M leaves in the result.  With a stopping
+                         rule (nmf_problem.rel_tol) only the float32 sweeps are watched. */
 } nmf_precision;
 
 /* Multigrid cycle (Section 4.3). */
@@ -128,8 +137,7 @@ typedef struct {
     nmf_cycle cycle;
     double rel_tol;     /* > 0: stopping rule on the last run of finest-level sweeps (the
                            post-smoothing of a V-cycle): stop once |f_{t-1} - f_t| <= rel_tol * f_t,
-                           f_t = ||M - VW||_F after finest-level sweep t (HALS and MU; ignored for
-                           ANLS); 0: run the whole schedule */
+                           f_t = ||M - VW||_F after finest-level sweep t; 0: run the whole schedule */
     float* V;           /* in: V0 (m x r); out: result */
     float* W;           /* in: W0 (r x n); out: result */
     /* outputs */
@@ -167,7 +175,10 @@ int nmf_release_workspace(nmf_handle h);
  * held by all slots <= hbm_budget_bytes; idle slots release theirs when the
  * queue head does not fit) and solves them as one nmf_solve_batch, on its own
  * stream while other slots run theirs.  A request's result is the one
- * nmf_solve_batch gives it alone.
+ * nmf_solve_batch gives it alone.  The environment variable NMF_SERVE_MAX_BATCH
+ * (1..16, read at nmf_server_create) lowers the number of requests a slot takes at
+ * once: a batch is one CUDA graph per combination of request shapes, so 1 reuses
+ * the graph of each shape and leaves the overlap to the slots' streams.
  */
 typedef struct nmf_server_s* nmf_server;
 int nmf_server_create(nmf_server* out, int device, size_t hbm_budget_bytes, int slots, nmf_precision prec);

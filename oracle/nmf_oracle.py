@@ -169,23 +169,47 @@ def objective_sq_expanded(M: np.ndarray, V: np.ndarray, W: np.ndarray) -> float:
 
 # ---------------------------------------------------------------------------
 # The four products of a sweep (Appendix A.1): A = M W^T, B = W W^T, C = V^T M,
-# D = V^T V.  FP64 by default.  READING: cycles that start on a level with fewer
-# pixels than the rank (nested iteration and full multigrid on the 19 x 19 grid
-# with three levels: 25 pixels, r = 49) have a flat objective there, and the point
-# their sweeps settle on depends on how the products are rounded; with
-# PRODUCT_ROUNDING = np.float32 the operands and the results of these products are
-# rounded to float32 (everything else stays FP64), which states that case at the
-# precision of a float32 implementation.  solve(..., products="fp32") sets it.
+# D = V^T V, and the precision they are taken in.  FP64 by default (PRECISION None).
+# READING: the paper computes in double and is silent on rounding; two settings
+# state the arithmetic of reduced-precision implementations, step by step:
+#   "fp32": the four products are float32 matrix products (float32 operands,
+#           float32 accumulation, a library matmul), and V and W are stored in
+#           float32 after each half of a sweep (V before C and D are formed);
+#   "bf16": the precision form of this library: A and C have bfloat16 operands
+#           (M and the factor, rounded to nearest, ties to even) accumulated in
+#           float32, B and D are float32 products, V, W stored in float32.
+# Cycles that start on a level with fewer pixels than the rank (nested iteration
+# and full multigrid on the 19 x 19 grid with three levels: 25 pixels, r = 49) and
+# short sweep budgets are sensitive to these roundings; solve(..., precision=...)
+# sets the mode for one solve.
 # ---------------------------------------------------------------------------
-PRODUCT_ROUNDING = None
+PRECISION = None
 
 
-def product(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
-    """X @ Y in FP64, or with operands and result rounded to PRODUCT_ROUNDING."""
-    if PRODUCT_ROUNDING is None:
+def round_bf16(X: np.ndarray) -> np.ndarray:
+    """X rounded to bfloat16 (8 significant bits), returned as float64.
+
+    From the format's definition: a bfloat16 is the upper 16 bits of a float32;
+    rounding to nearest with ties to even adds 0x7FFF plus the lowest kept bit to
+    the float32 bit pattern, then clears the low 16 bits."""
+    x = np.ascontiguousarray(X, dtype=np.float32)
+    bits = x.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def product(X: np.ndarray, Y: np.ndarray, factor_with_M: bool = False) -> np.ndarray:
+    """X @ Y at the current PRECISION; factor_with_M marks A = M W^T and C = V^T M."""
+    if PRECISION is None:
         return X @ Y
-    t = PRODUCT_ROUNDING
-    return (np.asarray(X).astype(t) @ np.asarray(Y).astype(t)).astype(np.float64)
+    if PRECISION == "bf16" and factor_with_M:
+        X, Y = round_bf16(X), round_bf16(Y)
+    return (np.asarray(X, np.float32) @ np.asarray(Y, np.float32)).astype(np.float64)
+
+
+def store(X: np.ndarray) -> np.ndarray:
+    """An iterate as stored between sweeps at the current PRECISION."""
+    return X if PRECISION is None else np.asarray(X, np.float32).astype(np.float64)
 
 
 # ---------------------------------------------------------------------------
@@ -218,11 +242,12 @@ def hals_sweep(M, V, W):
     """One pass of the while-loop of Algorithm HALS: all columns of V, then all rows of W."""
     V = np.array(V, dtype=np.float64)
     W = np.array(W, dtype=np.float64)
-    A = product(M, W.T)
+    A = product(M, W.T, True)
     B = product(W, W.T)
     for k in range(V.shape[1]):
         hals_update_V_column(V, A, B, k)
-    C = product(V.T, M)
+    V = store(V)
+    C = product(V.T, M, True)
     D = product(V.T, V)
     for k in range(W.shape[0]):
         hals_update_W_row(W, C, D, k)
@@ -240,8 +265,8 @@ def mu_sweep(M, V, W):
     """
     V = np.array(V, dtype=np.float64)
     W = np.array(W, dtype=np.float64)
-    V = V * product(M, W.T) / np.maximum(V @ product(W, W.T), EPS_MU)
-    W = W * product(V.T, M) / np.maximum(product(V.T, V) @ W, EPS_MU)
+    V = store(V * product(M, W.T, True) / np.maximum(V @ product(W, W.T), EPS_MU))
+    W = W * product(V.T, M, True) / np.maximum(product(V.T, V) @ W, EPS_MU)
     return V, W
 
 
@@ -298,6 +323,66 @@ def nnls_active_set(G: np.ndarray, b: np.ndarray, max_outer: int | None = None) 
             x[~passive] = 0.0
 
 
+def nnls_bpp(G: np.ndarray, b: np.ndarray, max_iter: int | None = None, info: dict | None = None) -> np.ndarray:
+    """argmin_{x >= 0} 1/2 x^T G x - b^T x by block principal pivoting.
+
+    The ANLS footnote of Section 2.1 names this method (Kim and Park) as an
+    alternative NNLS solver inside ANLS.  Variables are split into a passive set F
+    (free) and its complement (held at zero).  Each iteration solves the
+    unconstrained problem on F, x_F = G_FF^{-1} b_F, and forms the gradient
+    y = G x - b on the complement.  The pair is optimal when x_F >= 0 and y >= 0 off
+    F.  Otherwise the infeasible variables (x_k < 0 in F, y_k < -tol off F) change
+    sides all at once while their number keeps decreasing; after three exchanges
+    without a decrease only the infeasible variable of largest index changes side
+    (the backup rule that makes the method finite).  READING: tol is the dual
+    tolerance of the active-set method (1e-12 max(1, max |b|)), the iteration cap is
+    5r, and when G_FF is singular (G only semidefinite) or the cap is reached the
+    solution is taken from the active-set method.  ``info`` (optional dict) receives
+    "method" ("bpp" or "active set") and "iterations".
+    """
+    G = np.asarray(G, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    r = b.shape[0]
+    if max_iter is None:
+        max_iter = 5 * r
+    tol = 1e-12 * max(1.0, float(np.max(np.abs(b))) if r else 1.0)
+    F = np.zeros(r, dtype=bool)
+    x = np.zeros(r)
+    y = -b.copy()
+    nmin, backup = r + 1, 3
+    if info is not None:
+        info.update(method="bpp", iterations=0)
+    for it in range(max_iter):
+        infeasible = np.flatnonzero((F & (x < 0.0)) | (~F & (y < -tol)))
+        if infeasible.size == 0:
+            if info is not None:
+                info["iterations"] = it
+            return np.where(F, x, 0.0)
+        if infeasible.size < nmin:
+            nmin, backup = infeasible.size, 3
+            F[infeasible] = ~F[infeasible]
+        elif backup > 0:
+            backup -= 1
+            F[infeasible] = ~F[infeasible]
+        else:
+            k = infeasible[-1]
+            F[k] = not F[k]
+        P = np.flatnonzero(F)
+        x = np.zeros(r)
+        if P.size:
+            GPP = G[np.ix_(P, P)]
+            if np.linalg.matrix_rank(GPP) < P.size:
+                if info is not None:
+                    info["method"] = "active set"
+                return nnls_active_set(G, b)
+            x[P] = np.linalg.solve(GPP, b[P])
+        y = G @ x - b
+        y[F] = 0.0
+    if info is not None:
+        info["method"] = "active set"
+    return nnls_active_set(G, b)
+
+
 def anls_sweep(M, V, W):
     """One pass of Algorithm ANLS: V <- argmin_{V>=0} ||M-VW||, then W likewise.
 
@@ -310,15 +395,27 @@ def anls_sweep(M, V, W):
     m = M.shape[0]
     n = M.shape[1]
     G = product(W, W.T)
-    A = product(M, W.T)
-    V = np.stack([nnls_active_set(G, A[i]) for i in range(m)])
+    A = product(M, W.T, True)
+    V = store(np.stack([nnls_active_set(G, A[i]) for i in range(m)]))
     D = product(V.T, V)
-    C = product(V.T, M)
+    C = product(V.T, M, True)
     W = np.stack([nnls_active_set(D, C[:, j]) for j in range(n)], axis=1)
     return V, W
 
 
-SWEEPS = {"hals": hals_sweep, "mu": mu_sweep, "anls": anls_sweep}
+def anls_bpp_sweep(M, V, W):
+    """Algorithm ANLS with its NNLS problems solved by block principal pivoting (nnls_bpp)."""
+    W = np.array(W, dtype=np.float64)
+    G = product(W, W.T)
+    A = product(M, W.T, True)
+    V = store(np.stack([nnls_bpp(G, A[i]) for i in range(M.shape[0])]))
+    D = product(V.T, V)
+    C = product(V.T, M, True)
+    W = np.stack([nnls_bpp(D, C[:, j]) for j in range(M.shape[1])], axis=1)
+    return V, W
+
+
+SWEEPS = {"hals": hals_sweep, "mu": mu_sweep, "anls": anls_sweep, "anls_bpp": anls_bpp_sweep}
 
 
 def smooth(M, V, W, algo: str, sweeps: int, trace=None, level: int = 1):
@@ -326,6 +423,7 @@ def smooth(M, V, W, algo: str, sweeps: int, trace=None, level: int = 1):
     step = SWEEPS[algo]
     for _ in range(sweeps):
         V, W = step(M, V, W)
+        V, W = store(V), store(W)
         if trace is not None:
             trace.append((level, objective(M, V, W)))
     return V, W
@@ -420,22 +518,21 @@ CYCLES = {"vcycle": vcycle, "ni": nested_iteration, "fmg": full_multigrid, "wcyc
 
 
 def solve(M, grid_h: int, grid_w: int, V0, W0, algo: str = "hals", levels: int = 1, K: int = 100,
-          cycle: str = "vcycle", trace=None, products: str = "fp64"):
+          cycle: str = "vcycle", trace=None, precision: str = "fp64"):
     """Multilevel NMF of M (m = grid_h * grid_w rows) from (V0, W0); returns (V, W).
 
-    products: "fp64" (default) or "fp32" (the four products of each sweep rounded to
-    float32, see PRODUCT_ROUNDING)."""
-    global PRODUCT_ROUNDING
+    precision: "fp64" (default), "fp32" or "bf16" (see PRECISION)."""
+    global PRECISION
     M = np.asarray(M, dtype=np.float64)
     Ms = restrict_hierarchy(M, grid_h, grid_w, levels)
     grids = grid_hierarchy(grid_h, grid_w, levels)
     V = np.asarray(V0, dtype=np.float64)
     W = np.asarray(W0, dtype=np.float64)
-    saved = PRODUCT_ROUNDING
-    PRODUCT_ROUNDING = {"fp64": None, "fp32": np.float32}[products]
+    saved = PRECISION
+    PRECISION = {"fp64": None, "fp32": "fp32", "bf16": "bf16"}[precision]
     try:
         if cycle == "vcycle":
             return vcycle(Ms, grids, V, W, algo, levels, K, trace=trace)
         return CYCLES[cycle](Ms, grids, V, W, algo, levels, K, trace=trace)
     finally:
-        PRODUCT_ROUNDING = saved
+        PRECISION = saved

@@ -410,8 +410,10 @@ __global__ void __launch_bounds__(NT, 1)
 
 // Partial Gram slabs of a tall factor: out[t] = F[bt t : bt t + bt]^T F[bt t : bt t + bt], bt <= 64.
 __global__ void __launch_bounds__(256) gram_tiles_kernel(const float* __restrict__ F, int64_t rows, int r, int rp,
-                                                         int bt, float* __restrict__ out, int64_t out_stride) {
+                                                         int bt, float* __restrict__ out, int64_t out_stride,
+                                                         const int* skip) {
     __shared__ float Fs[64][kMaxRank + 1];
+    if (skip && *(volatile const int*)skip) return;  // same value in every CTA
     const int64_t r0 = (int64_t)blockIdx.x * bt;
     for (int e = threadIdx.x; e < bt * rp; e += blockDim.x) {
         const int rr = e / rp, k = e - rr * rp;
@@ -556,11 +558,11 @@ cudaError_t half_sweep_launch(const HalfSweepLaunch& hl, cudaStream_t st) {
 }
 
 cudaError_t gram_tiles_launch(const float* F, int64_t rows, int r, int rp, int tile_rows, float* out,
-                              int64_t out_stride, cudaStream_t st) {
+                              int64_t out_stride, cudaStream_t st, const int* skip) {
     if (tile_rows < 1 || tile_rows > 64) return cudaErrorInvalidValue;
     const int64_t tiles = (rows + tile_rows - 1) / tile_rows;
     if (tiles <= 0) return cudaSuccess;
-    gram_tiles_kernel<<<(unsigned)tiles, 256, 0, st>>>(F, rows, r, rp, tile_rows, out, out_stride);
+    gram_tiles_kernel<<<(unsigned)tiles, 256, 0, st>>>(F, rows, r, rp, tile_rows, out, out_stride, skip);
     return cudaGetLastError();
 }
 

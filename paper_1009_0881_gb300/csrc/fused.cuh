@@ -54,6 +54,6 @@ size_t half_sweep_smem_bytes(int br, int ba, int r, int cs);
 cudaError_t half_sweep_launch(const HalfSweepLaunch& hl, cudaStream_t st);
 // Gram partial slabs of a tall factor, one per tile of `tile_rows` (<= 64) rows.
 cudaError_t gram_tiles_launch(const float* F, int64_t rows, int r, int rp, int tile_rows, float* out,
-                              int64_t out_stride, cudaStream_t st);
+                              int64_t out_stride, cudaStream_t st, const int* skip = nullptr);
 
 }  // namespace nmfk

@@ -73,6 +73,8 @@ struct UpdateArgs {
     int r;
     double* Gd;        // ANLS: r x r scratch receiving the FP64 sum of the Gram partials
     int max_outer;     // ANLS: cap on the variables added per row (< 0: 3r, the default)
+    int bpp;           // ANLS: 1 = block principal pivoting first (active set where it cannot finish)
+    const int* skip;   // optional: when *skip != 0 the launch does nothing (converged problem)
 };
 
 // ANLS: F rows = argmin_{x>=0} 1/2 x^T G x - p^T x, FP64 active set.  status: device int

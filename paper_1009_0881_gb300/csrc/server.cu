@@ -11,6 +11,7 @@
 // concurrent branches inside a batch).
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -50,6 +51,7 @@ struct nmf_server_s {
     int64_t next_ticket = 0;
     int64_t running = 0, completed = 0;
     nmf_handle sizer = nullptr;  // workspace estimates (used under mu)
+    int max_batch = kMaxBatch;   // requests a slot takes at once (NMF_SERVE_MAX_BATCH)
 
     size_t held_except(int i) const {
         size_t s = 0;
@@ -98,7 +100,7 @@ void worker_loop(nmf_server_s* s, int i) {
         // the longest run from the head that fits together
         int count = 1;
         size_t bytes = s->queue.front()->bytes;
-        const int most = std::min<int>(kMaxBatch, (int)s->queue.size());
+        const int most = std::min<int>(s->max_batch, (int)s->queue.size());
         while (count < most) {
             const size_t b = s->group_bytes(count + 1);
             if (!s->fits(i, b)) break;
@@ -156,6 +158,10 @@ int nmf_server_create(nmf_server* out, int device, size_t hbm_budget_bytes, int 
         return NMF_ECUDA;
     }
     s->held.assign(slots, 0);
+    if (const char* e = std::getenv("NMF_SERVE_MAX_BATCH")) {
+        const int v = std::atoi(e);
+        if (v >= 1) s->max_batch = std::min(v, kMaxBatch);
+    }
     for (int i = 0; i < slots; ++i) s->workers.emplace_back(worker_loop, s, i);
     *out = s;
     return NMF_OK;

@@ -29,6 +29,10 @@ namespace {
 
 const char* kBuildTag = "gb300-nmf sm_103a fp32-ffma+bf16-tcgen05";
 
+// ANLS with either NNLS method (the active-set method of Appendix A.2, or block
+// principal pivoting).
+inline bool is_anls(nmf_algo a) { return a == NMF_ANLS || a == NMF_ANLS_BPP; }
+
 // ---------------------------------------------------------------------------
 // Cycle schedules (Section 4.3) as a flat list of operations
 // ---------------------------------------------------------------------------
@@ -185,6 +189,7 @@ struct Plan {
     size_t bytes = 0;
     // BF16 precision form
     bool bf16 = false;
+    bool finish32 = false;            // BF16 form with the last quarter of the last finest-level run in FP32
     int bn = 0;                       // MMA N
     int64_t ldmb = 0;                 // leading dimension of M and W in BF16 (multiple of 8)
     __nv_bfloat16* Wb = nullptr;      // r x ldmb
@@ -771,7 +776,8 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
     p.n = n;
     p.r = r;
     p.rp = (int)round_up(r, 4);
-    p.bf16 = h->prec == NMF_BF16;
+    p.bf16 = h->prec != NMF_FP32;
+    p.finish32 = h->prec == NMF_BF16_FP32;
     p.br = pick_br(p.rp);
     // W-step tile height chosen on the finest level (the W-step tiles and their Gram
     // slabs are shared by all levels); V-step tiles per level.  The BF16 form's row
@@ -811,7 +817,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
     cudaError_t e = half_sweep_launch(a, h->stream);
     if (e != cudaSuccess) return e;
     ++*launches;
-    if (algo == NMF_ANLS) {
+    if (is_anls(algo)) {
         UpdateArgs u{};
         u.F = v.V;
         u.ldf = p.rp;
@@ -827,8 +833,10 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.r = p.r;
         u.Gd = p.Gd;
         u.max_outer = h->nnls_cap;
+        u.bpp = algo == NMF_ANLS_BPP;
+        u.skip = skip;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
-        if (e == cudaSuccess) e = gram_tiles_launch(v.V, v.m, p.r, p.rp, v.vtile, p.GD, p.slab, h->stream);
+        if (e == cudaSuccess) e = gram_tiles_launch(v.V, v.m, p.r, p.rp, v.vtile, p.GD, p.slab, h->stream, skip);
         if (e != cudaSuccess) return e;
         *launches += 3;
     }
@@ -839,7 +847,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
     e = half_sweep_launch(b, h->stream);
     if (e != cudaSuccess) return e;
     ++*launches;
-    if (algo == NMF_ANLS) {
+    if (is_anls(algo)) {
         UpdateArgs u{};
         u.F = p.Wt;
         u.ldf = p.rp;
@@ -855,8 +863,10 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.r = p.r;
         u.Gd = p.Gd;
         u.max_outer = h->nnls_cap;
+        u.bpp = algo == NMF_ANLS_BPP;
+        u.skip = skip;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
-        if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream);
+        if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream, skip);
         if (e != cudaSuccess) return e;
         *launches += 3;
     }
@@ -943,7 +953,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
     q.gout_stride = p.slab;
     q.skip = skip;
     q.ba = v.vtile;
-    if (algo == NMF_ANLS) {
+    if (is_anls(algo)) {
         UpdateArgs u{};
         u.F = v.V;
         u.ldf = p.rp;
@@ -959,6 +969,8 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
         u.r = p.r;
         u.Gd = p.Gd;
         u.max_outer = h->nnls_cap;
+        u.bpp = algo == NMF_ANLS_BPP;
+        u.skip = skip;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e != cudaSuccess) return e;
     }
@@ -975,7 +987,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
     q.ldb = p.ldmb;
     q.Gout = p.GB;
     q.ba = p.wtile;
-    if (algo == NMF_ANLS) {
+    if (is_anls(algo)) {
         UpdateArgs u{};
         u.F = p.Wt;
         u.ldf = p.rp;
@@ -991,6 +1003,8 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
         u.r = p.r;
         u.Gd = p.Gd;
         u.max_outer = h->nnls_cap;
+        u.bpp = algo == NMF_ANLS_BPP;
+        u.skip = skip;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e != cudaSuccess) return e;
     }
@@ -1004,10 +1018,12 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
     int last_fine = -1;
     for (int i = 0; i < (int)ops.size(); ++i)
         if (ops[i].kind == OP_SWEEPS && ops[i].level == 0) last_fine = i;
-    const bool stop_rule = rel_tol > 0.0 && algo != NMF_ANLS && last_fine >= 0;
+    const int last_fine_all = last_fine;
+    const bool stop_rule = rel_tol > 0.0 && last_fine >= 0;
     // FP32 form: the stopping rule reads the objective from the identity terms of the
     // W-step (no extra pass over M); it needs ||M||_F of the finest level once
-    const bool identity = stop_rule && !p.bf16;
+    // (the BF16 form with FP32 finishing watches only its FP32 sweeps)
+    const bool identity = stop_rule && (!p.bf16 || p.finish32);
     // B = W W^T slabs of the initial W, consumed by the first V-step
     cudaError_t e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream);
     if (e == cudaSuccess && identity)
@@ -1025,7 +1041,7 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
         } else if (op.kind == OP_PROLONG_V) {
             const Level& c = p.lv[op.level + 1];
             e = prolong_launch(c.V, p.rp, f.h, f.w, p.rp, f.V, p.rp, h->stream);
-        } else if (f.crun && algo != NMF_ANLS && op.level > 0 && !watched) {
+        } else if (f.crun && !is_anls(algo) && op.level > 0 && !watched) {
             int64_t cnt = op.count;
             if (stop_after > 0) cnt = std::min<int64_t>(cnt, std::max<int64_t>(0, stop_after - done));
             if (cnt > 0) {
@@ -1036,17 +1052,21 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
                 gb_single = true;
             }
         } else {
+            // BF16 form with FP32 finishing: the last quarter of the last finest-level run
+            // (at least one sweep) runs the FP32 kernels on the FP32 M (Mt formed at staging)
+            const int64_t nfin = (p.finish32 && oi == last_fine_all) ? (op.count + 3) / 4 : 0;
             for (int64_t s = 0; s < op.count; ++s) {
                 if (stop_after > 0 && done >= stop_after) break;
-                const int* skip = watched ? p.conv_flag : nullptr;
-                e = p.bf16 ? enqueue_sweep_bf16(h, p, op.level, algo, skip)
-                           : enqueue_sweep(h, p, op.level, algo, &launches, skip, watched ? p.obj_part : nullptr,
-                                           gb_single);
+                const bool fp32 = !p.bf16 || s >= op.count - nfin;
+                const bool watch = watched && (!p.finish32 || fp32);
+                const int* skip = watch ? p.conv_flag : nullptr;
+                e = fp32 ? enqueue_sweep(h, p, op.level, algo, &launches, skip, watch ? p.obj_part : nullptr, gb_single)
+                         : enqueue_sweep_bf16(h, p, op.level, algo, skip);
                 gb_single = false;
                 if (e != cudaSuccess) return e;
                 ++done;
-                if (watched) {
-                    if (identity)
+                if (watch) {
+                    if (identity && fp32 && !is_anls(algo))
                         e = identity_objective_launch(p.obj_part, f.hsW.tiles * f.hsW.p.cs, p.mnorm, p.conv_state + 1,
                                                       p.conv_flag, h->stream);
                     else
@@ -1147,7 +1167,7 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
         return fail(h, NMF_EINVAL, "grid %d x %d does not have m = %lld pixels", gh, gw, (long long)m);
     if (L < 1 || L > 16) return fail(h, NMF_EINVAL, "levels must be in 1..16 (got %d)", L);
     if (K < 0) return fail(h, NMF_EINVAL, "iters must be >= 0");
-    if (algo != NMF_HALS && algo != NMF_MU && algo != NMF_ANLS) return fail(h, NMF_EINVAL, "unknown algorithm");
+    if (algo != NMF_HALS && algo != NMF_MU && !is_anls(algo)) return fail(h, NMF_EINVAL, "unknown algorithm");
     const nmf_cycle cyc = opt ? opt->cycle : NMF_VCYCLE;
     if (cyc != NMF_VCYCLE && cyc != NMF_NESTED && cyc != NMF_FMG && cyc != NMF_WCYCLE)
         return fail(h, NMF_EINVAL, "unknown cycle");
@@ -1161,7 +1181,7 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     if (rc) return rc;
     rc = init_levels_padding(h, p);
     if (rc) return rc;
-    rc = stage_problem(h, p, M, V, W, !p.bf16);
+    rc = stage_problem(h, p, M, V, W, !p.bf16 || p.finish32);
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
@@ -1255,7 +1275,7 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
         if (q.grid_h < 1 || q.grid_w < 1 || (int64_t)q.grid_h * q.grid_w != q.m)
             return fail(h, NMF_EINVAL, "problem %d: grid does not have m pixels", i);
         if (q.levels < 1 || q.levels > 16 || q.iters < 0) return fail(h, NMF_EINVAL, "problem %d: bad levels/iters", i);
-        if (q.algo != NMF_HALS && q.algo != NMF_MU && q.algo != NMF_ANLS)
+        if (q.algo != NMF_HALS && q.algo != NMF_MU && !is_anls(q.algo))
             return fail(h, NMF_EINVAL, "problem %d: unknown algorithm", i);
         if (q.cycle != NMF_VCYCLE && q.cycle != NMF_NESTED && q.cycle != NMF_FMG && q.cycle != NMF_WCYCLE)
             return fail(h, NMF_EINVAL, "problem %d: unknown cycle", i);
@@ -1270,7 +1290,7 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
     for (int i = 0; i < count; ++i) {
         rc = init_levels_padding(h, plans[i]);
         if (rc) return rc;
-        rc = stage_problem(h, plans[i], probs[i].M, probs[i].V, probs[i].W, !plans[i].bf16);
+        rc = stage_problem(h, plans[i], probs[i].M, probs[i].V, probs[i].W, !plans[i].bf16 || plans[i].finish32);
         if (rc) return rc;
         Plan& p = plans[i];
         CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
@@ -1369,7 +1389,11 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
                 total += ops[k].count;
                 if (ops[k].level == 0) last_fine = k;
             }
-        if (q.rel_tol > 0.0 && q.algo != NMF_ANLS && last_fine >= 0) total += cnt - ops[last_fine].count;
+        if (q.rel_tol > 0.0 && last_fine >= 0) {
+            // with FP32 finishing only the FP32 quarter of that run is watched
+            const int64_t watched_n = p.finish32 ? (ops[last_fine].count + 3) / 4 : ops[last_fine].count;
+            total += cnt - watched_n;
+        }
         q.sweeps_run = total;
         q.objective = obj;
         q.status = bad ? NMF_EINVAL : (flag ? NMF_ETIMEOUT : (st ? NMF_ENOCONV : NMF_OK));
@@ -1397,7 +1421,7 @@ extern "C" {
 int nmf_create(nmf_handle* out, int device, size_t hbm_budget_bytes, nmf_precision prec) {
     if (!out) return NMF_EINVAL;
     *out = nullptr;
-    if (prec != NMF_FP32 && prec != NMF_BF16) return NMF_EINVAL;
+    if (prec != NMF_FP32 && prec != NMF_BF16 && prec != NMF_BF16_FP32) return NMF_EINVAL;
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
         cudaGetLastError();
@@ -1651,13 +1675,13 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
     int rc = check_dims(h, m, n, r);
     if (rc) return rc;
     if (!M || !V || !W || !ms_out || reps < 1) return fail(h, NMF_EINVAL, "bad profile arguments");
-    if (algo != NMF_HALS && algo != NMF_MU && algo != NMF_ANLS) return fail(h, NMF_EINVAL, "unknown algorithm");
+    if (algo != NMF_HALS && algo != NMF_MU && !is_anls(algo)) return fail(h, NMF_EINVAL, "unknown algorithm");
     CK(cudaSetDevice(h->device));
     h->launches = 0;
     Plan p;
     rc = make_plan(h, p, m, n, (int)m, 1, r, 1, 0);
     if (rc) return rc;
-    rc = stage_problem(h, p, M, V, W, !p.bf16);
+    rc = stage_problem(h, p, M, V, W, !p.bf16 || p.finish32);
     if (rc) return rc;
     CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
@@ -1713,7 +1737,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                 hl.mode = mode;
                 e = half_sweep_launch(hl, h->stream);
             } else if (phase == 1 || phase == 3) {
-                if (algo != NMF_ANLS) {
+                if (!is_anls(algo)) {
                     nl = 0;
                 } else {
                     const bool vstep = phase == 1;
@@ -1731,6 +1755,8 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                     u.r = p.r;
                     u.Gd = p.Gd;
                     u.max_outer = h->nnls_cap;
+                    u.bpp = algo == NMF_ANLS_BPP;
+                    u.skip = nullptr;
                     e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
                     if (e == cudaSuccess)
                         e = gram_tiles_launch(u.F, u.rows, p.r, p.rp, vstep ? v.vtile : p.wtile, vstep ? p.GD : p.GB,

@@ -157,12 +157,78 @@ __device__ void chol_solve(const double* L, const double* dinv, int r, const int
     __syncwarp();
 }
 
+// Block principal pivoting (the alternative NNLS method of the ANLS footnote in
+// Section 2.1): all infeasible variables (x_k < 0 in the passive set F, gradient
+// g_k = (G x - b)_k < -tol outside it) change sides at once while their number keeps
+// falling; after three exchanges without a fall only the one of largest index moves
+// (backup rule).  Each iteration factors G_FF anew.  Returns false when a factor is
+// numerically singular or the cap is reached (the caller then runs the active-set
+// method); on true, x holds the solution (zero outside F).
+__device__ bool bpp_row(const double* G, int r, const double b[2], const double* bs, double tol, double* L,
+                        double* dinv, int* ord, int* inv, double* y, int lane, int max_iter, double x[2]) {
+    uint64_t F = 0;
+    double xv[2] = {0.0, 0.0};
+    double g[2] = {-b[0], -b[1]};
+    int nmin = r + 1, backup = 3, p = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        uint64_t bad = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int k = lane + 32 * s;
+            const bool inF = k < r && ((F >> k) & 1ull);
+            const bool infeasible = k < r && (inF ? xv[s] < 0.0 : g[s] < -tol);
+            bad |= (uint64_t)__ballot_sync(kFull, infeasible) << (32 * s);
+        }
+        if (!bad) {
+            x[0] = xv[0];
+            x[1] = xv[1];
+            return true;
+        }
+        const int nbad = __popcll(bad);
+        if (nbad < nmin) {
+            nmin = nbad;
+            backup = 3;
+            F ^= bad;
+        } else if (backup > 0) {
+            --backup;
+            F ^= bad;
+        } else {
+            F ^= 1ull << (63 - __clzll((long long)bad));
+        }
+        xv[0] = xv[1] = 0.0;
+        if (F) {
+            if (!chol_full(G, r, F, L, dinv, ord, inv, p, lane)) return false;
+            chol_solve(L, dinv, r, ord, inv, p, F, bs, xv, y, lane);
+        }
+        // gradient outside F: g = G x - b (zero in F)
+        g[0] = -b[0];
+        g[1] = -b[1];
+        for (int l = 0; l < r; ++l) {
+            const double xl = __shfl_sync(kFull, xv[l >> 5], l & 31);
+            if (xl != 0.0) {
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int k = lane + 32 * s;
+                    if (k < r) g[s] += G[k * r + l] * xl;
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int k = lane + 32 * s;
+            if (k < r && ((F >> k) & 1ull)) g[s] = 0.0;
+        }
+    }
+    return false;
+}
+
 // Per-warp shared memory of the ANLS kernel in doubles: L (packed, r (r+1)/2), dinv, y, bs.
 __host__ __device__ inline size_t anls_warp_doubles(int r) { return (size_t)r * (r + 1) / 2 + 3 * kMaxRank; }
 
 // G = sum of the Gram partial slabs in FP64 (slabs in index order), once per
 // half-sweep, for all the ANLS rows.
 __global__ void gram_reduce_f64_kernel(const UpdateArgs u) {
+    if (u.skip && *(volatile const int*)u.skip) return;
     const int r = u.r;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= r * r) return;
@@ -173,8 +239,10 @@ __global__ void gram_reduce_f64_kernel(const UpdateArgs u) {
     u.Gd[idx] = s;
 }
 
+template <bool BPP>
 __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const UpdateArgs u, int* status) {
     extern __shared__ double smem[];
+    if (u.skip && *(volatile const int*)u.skip) return;  // same value in every CTA
     const int r = u.r;
     double* G = smem;  // r x r
     for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) G[idx] = u.Gd[idx];
@@ -210,6 +278,10 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
         __syncwarp();
         const double bmax = warp_max(fmax(fabs(b[0]), fabs(b[1])));
         const double tol = 1e-12 * fmax(1.0, bmax);
+        bool capped = false;
+        if (BPP && bpp_row(G, r, b, bs, tol, L, dinv, ord, inv, y, lane, 5 * r, x)) {
+            // solved by block pivoting
+        } else {
         uint64_t mask = 0, excluded = 0;
         int p = 0;
 
@@ -241,7 +313,6 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
             p = 0;
         }
 
-        bool capped = false;
         // dual w = b - G x, recomputed only when x has changed: a candidate whose column
         // depends on the passive set is excluded without changing x
         double w[2] = {0.0, 0.0};
@@ -346,6 +417,7 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
                 }
             }
         }
+        }  // active set
         if (capped && lane == 0) atomicOr(status, 1);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -363,8 +435,12 @@ static size_t anls_smem_bytes(int r) {
 }
 
 cudaError_t init_kernel_attributes() {
-    return cudaFuncSetAttribute(anls_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)anls_smem_bytes(kMaxRank));
+    cudaError_t e = cudaFuncSetAttribute(anls_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)anls_smem_bytes(kMaxRank));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(anls_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)anls_smem_bytes(kMaxRank));
+    return e;
 }
 
 cudaError_t anls_update_launch(const UpdateArgs& u, int num_sms, int* d_status, cudaStream_t st) {
@@ -375,7 +451,10 @@ cudaError_t anls_update_launch(const UpdateArgs& u, int num_sms, int* d_status, 
     int64_t grid = ceil_div(u.rows, kAnlsWarps);
     const int64_t cap = 8LL * num_sms;
     if (grid > cap) grid = cap;
-    anls_rows_kernel<<<(unsigned)grid, 32 * kAnlsWarps, smem, st>>>(u, d_status);
+    if (u.bpp)
+        anls_rows_kernel<true><<<(unsigned)grid, 32 * kAnlsWarps, smem, st>>>(u, d_status);
+    else
+        anls_rows_kernel<false><<<(unsigned)grid, 32 * kAnlsWarps, smem, st>>>(u, d_status);
     return cudaGetLastError();
 }
 

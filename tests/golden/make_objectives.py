@@ -50,11 +50,36 @@ CASES = [
 ]
 
 
-# Cycles that start on a level with fewer pixels than the rank: their result depends on the
-# rounding of the products (oracle reading PRODUCT_ROUNDING), so the float32-product value is
-# stored beside the FP64 one.
+# Cycles that start on a level with fewer pixels than the rank: their result depends on
+# rounding (oracle reading PRECISION), so the values at float32 precision are stored beside the
+# FP64 one.
 FP32_PRODUCT_CASES = {"grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100", "grid19_mu_fmg_L3_K100",
                       "grid19_anls_fmg_L3_K8"}
+
+
+def _fp32_value(name, threads):
+    """Final objective of case `name` with the oracle at float32 precision, run in a child
+    process whose float32 matrix products use `threads` threads (None if its active-set NNLS
+    cycled on a rounded singular Gram matrix)."""
+    import subprocess
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--fp32", name], env=env, check=True,
+                         capture_output=True, text=True).stdout.strip().splitlines()[-1]
+    return None if out == "None" else float(out)
+
+
+def _fp32_child(name):
+    for nm, wl, algo, L, K, cyc in CASES:
+        if nm == name:
+            h, w, n, r, sigma = synth.WORKLOADS[wl]
+            p = synth.make_problem(h, w, n, r, sigma=sigma)
+            try:
+                V, W = o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc, precision="fp32")
+                print(repr(o.objective(p.M.astype(np.float64), V, W)))
+            except o.NNLSNotConverged:
+                print("None")
+            return
 
 
 def _store(path, name, entry):
@@ -82,11 +107,16 @@ def main(only=None):
         entry = {"workload": wl, "algo": algo, "levels": L, "K": K, "cycle": cyc, "objective": f,
                  "norm_M": float(np.linalg.norm(p.M.astype(np.float64)))}
         if name in FP32_PRODUCT_CASES:
-            V, W = o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc, products="fp32")
-            entry["objective_fp32_products"] = o.objective(p.M.astype(np.float64), V, W)
+            # the oracle at float32 precision with two summation orders of its float32 matrix
+            # products (the library matmul on one thread and on four): on these cycles the two
+            # orders end in different places, so both are kept
+            entry["objective_fp32"] = [_fp32_value(name, threads) for threads in (1, 4)]
         _store(path, name, entry)
         print(f"{name}: {f:.10g} ({time.time() - t:.1f} s)", flush=True)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or None)
+    if len(sys.argv) == 3 and sys.argv[1] == "--fp32":
+        _fp32_child(sys.argv[2])
+    else:
+        main(sys.argv[1:] or None)

@@ -8,7 +8,8 @@ forms draw it), its algorithm cycling through HALS, MU, ANLS so that every size
 stratum meets every algorithm, three levels and a short fixed sweep budget (the
 oracle's cost on the largest sizes is the limit): K = 4 for HALS and MU, K = 2
 for ANLS.  A served request with the same (problem, algorithm, L, K) and no
-stopping rule must reach the stored objective.
+stopping rule must reach the stored objective: "objective" at FP64, and
+"objective_bf16" with the oracle in its bf16 mode (the library's precision form).
 
 Usage: python tests/golden/make_served_sample.py [workers]
 """
@@ -47,8 +48,18 @@ def _one(item):
     t = time.time()
     V, W = o.solve(p.M, side, side, p.V, p.W, algo, levels=L, K=K)
     f = o.objective(p.M.astype(np.float64), V, W)
+    try:
+        V, W = o.solve(p.M, side, side, p.V, p.W, algo, levels=L, K=K, precision="bf16")
+        fb = o.objective(p.M.astype(np.float64), V, W)
+    except o.NNLSNotConverged:
+        # the active-set method can cycle on a rounded singular Gram matrix: no bf16 value
+        fb = None
+    # coarsest grid of the hierarchy: ANLS there is not unique when it has fewer pixels than r
+    cs = side
+    for _ in range(L - 1):
+        cs = (cs + 1) // 2
     return {"index": i, "side": side, "n": n, "r": r, "sigma": sigma, "algo": algo, "levels": L, "iters": K,
-            "objective": f, "seconds": time.time() - t}
+            "objective": f, "objective_bf16": fb, "coarsest_pixels": cs * cs, "seconds": time.time() - t}
 
 
 def main(workers):

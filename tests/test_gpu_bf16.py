@@ -122,3 +122,58 @@ def test_bf16_anls_sweep_is_blockwise_optimal(hb):
     B = p.W.astype(np.float64) @ p.W.astype(np.float64).T
     Ve = np.stack([o.nnls_active_set(B, A[i]) for i in range(A.shape[0])])
     assert rel(V, Ve) < 1e-4
+
+
+@pytest.fixture(scope="module")
+def hf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1009_0881_gb300 import build
+    build.build()
+    with native.Handle(0, precision=native.NMF_BF16_FP32) as h:
+        yield h
+
+
+@pytest.mark.parametrize("name", ["grid112x92_hals_L3_K100", "grid256_hals_L3_K100", "grid19_mu_L3_K500"])
+def test_bf16_with_fp32_finishing_reaches_fp64_oracle(hf, name):
+    # BF16 sweeps, then the last quarter of the finest post-smoothing run in float32 on the
+    # float32 M: on the precision-form workloads (112 x 92 and 256 x 256 grids) the result is
+    # within 1e-3 of the FP64 oracle's objective, the bar of the float32 form, where BF16 alone
+    # stays up to 1.1e-2 away (the BF16 storage floor).  On the 19 x 19 HALS workload (r = 49)
+    # the 63 float32 sweeps do not finish the descent: it lands 7.2e-3 away (measured, not gated)
+    g = GOLDEN[name]
+    gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    V, W = p.V.copy(), p.W.copy()
+    hf.solve(p.M, gh, gw, V, W, g["algo"], levels=g["levels"], iters=g["K"], cycle=g["cycle"])
+    f = o.objective(p.M, V, W)
+    print(f"{name}: BF16 + FP32 finishing {f:.6g}, FP64 oracle {g['objective']:.6g}, "
+          f"rel {(f - g['objective']) / g['objective']:.2e}")
+    assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
+    assert (V >= 0).all() and (W >= 0).all()
+
+
+def test_bf16_with_fp32_finishing_batch_equals_alone(hf):
+    # the finishing form keeps the batched = standalone property, and the stopping rule
+    # watches its float32 sweeps only
+    reqs = []
+    for i, (gh, n, r) in enumerate([(16, 700, 10), (64, 1200, 33), (19, 2429, 49)]):
+        p = synth.make_problem(gh, gh, n, r, sigma=0.04 * gh if gh > 19 else 2.0, data_seed=60 + i)
+        reqs.append(dict(M=p.M, grid_h=gh, grid_w=gh, V=p.V.copy(), W=p.W.copy(), levels=3, iters=40))
+    alone = []
+    for d in reqs:
+        e = dict(d, V=d["V"].copy(), W=d["W"].copy())
+        (st, sweeps, obj), = hf.solve_batch([e])
+        assert st == 0 and sweeps == sum(native.schedule("vcycle", 3, 40))
+        alone.append(e)
+    res = hf.solve_batch(reqs)
+    for (st, sweeps, obj), d, e in zip(res, reqs, alone):
+        assert st == 0
+        np.testing.assert_array_equal(d["V"], e["V"])
+        np.testing.assert_array_equal(d["W"], e["W"])
+    ruled = [dict(d, V=d["V"].copy(), W=d["W"].copy(), rel_tol=0.5) for d in reqs]
+    res = hf.solve_batch(ruled)
+    total = sum(native.schedule("vcycle", 3, 40))
+    for st, sweeps, obj in res:
+        # a loose rule stops at the second watched sweep; the BF16 part always runs
+        assert st == 0 and sweeps == total - (40 // 2 + 3) // 4 + 2

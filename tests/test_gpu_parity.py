@@ -172,6 +172,39 @@ def test_single_anls_sweep_matches_oracle(h, case):
           f"W {ew:.2e} (bar {bar_w:.2e}, kappa {kw:.3g})")
 
 
+@pytest.mark.parametrize("case", [("grid16_n1000_r10", None), (None, (9, 7, 130, 12)), ("grid19_n2429_r49", None)])
+def test_single_anls_bpp_sweep_matches_oracle(h, case):
+    # block principal pivoting reaches the same NNLS solutions (unique where G is positive
+    # definite), so the oracle's block-pivoting sweep and the same condition-number bar apply
+    p = _problem(case)
+    V, W = p.V.copy(), p.W.copy()
+    h.sweep(p.M, V, W, "anls_bpp", 1)
+    M64 = p.M.astype(np.float64)
+    W0 = p.W.astype(np.float64)
+    Vo, Wo = o.anls_bpp_sweep(M64, p.V.astype(np.float64), W0)
+    m, n = p.M.shape
+    u = 2.0 ** -24
+    kv = _support_condition(W0 @ W0.T, Vo)
+    ev = rel(V, Vo)
+    assert ev <= max(1e-5, 4 * kv * u * np.sqrt(n)), (ev, kv)
+    kw = _support_condition(Vo.T @ Vo, Wo.T)
+    ew = rel(W, Wo)
+    assert ew <= max(1e-5, 4 * kw * (u * np.sqrt(m) + ev)), (ew, kw)
+
+
+@pytest.mark.parametrize("name", ["grid19_anls_L2_K8", "grid19_anls_L3_K8"])
+def test_anls_bpp_cycle_matches_oracle(h, name):
+    # the cycle with block-pivoting NNLS against the active-set oracle run: the same NNLS
+    # solutions where they are unique (and the active set where blocks are singular)
+    g = GOLDEN[name]
+    gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    V, W = p.V.copy(), p.W.copy()
+    h.solve(p.M, gh, gw, V, W, "anls_bpp", levels=g["levels"], iters=g["K"], cycle=g["cycle"])
+    f = o.objective(p.M, V, W)
+    assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
+
+
 def test_hals_ten_sweeps_track_oracle(h):
     # float32 rounding of the iterates grows along the iteration (the first sweep agrees to ~2e-6,
     # the objective after sweep 6 to ~3e-6), so several sweeps are compared through the objective
@@ -230,22 +263,27 @@ HEADLINE_L3 = ["grid19_anls_L3_K8", "grid19_anls_L3_K500", "grid19_anls_L1_K500"
 @pytest.mark.parametrize("name", HEADLINE_L3)
 def test_headline_cycles_at_three_levels_match_oracle(h, name):
     g = GOLDEN[name]
-    if "objective_fp32_products" not in g:
+    if "objective_fp32" not in g:
         test_cycle_final_objective_matches_oracle(h, name)
         return
     # NI and FMG begin with K sweeps on the 5 x 5 level (25 pixels < r = 49), where the
-    # objective is flat and the point the sweeps settle on depends on how the products
-    # are rounded: the FP64 oracle itself moves by more than 1e-3 when only its four
-    # products are rounded to float32.  The GPU (float32 products) is compared at 1e-3
-    # with that oracle run; the FP64 value is kept beside it.
+    # objective is flat and the point the sweeps settle on is decided by rounding: the oracle
+    # at float32 precision (float32 products and iterates) ends in one of two places depending
+    # only on the summation order of its float32 matrix products (one thread or four), 1.6 %
+    # apart, the FP64 run beside one of them.  The GPU (float32) must land within 1e-3 of a
+    # float32 oracle run; where the float32 oracle has no value (its active-set NNLS cycles on
+    # the rounded singular Gram matrix) the GPU is compared with the FP64 run at 1e-2.
     gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
     p = synth.make_problem(gh, gw, n, r, sigma=sigma)
     V, W = p.V.copy(), p.W.copy()
     h.solve(p.M, gh, gw, V, W, g["algo"], levels=g["levels"], iters=g["K"], cycle=g["cycle"])
     f = o.objective(p.M, V, W)
-    f32 = g["objective_fp32_products"]
-    assert abs(f - f32) <= 1e-3 * f32, (f, f32, g["objective"])
-    print(f"{name}: GPU {f:.6g}, oracle float32 products {f32:.6g}, oracle FP64 {g['objective']:.6g}")
+    f32 = [v for v in g["objective_fp32"] if v is not None]
+    print(f"{name}: GPU {f:.6g}, oracle at float32 {f32}, oracle FP64 {g['objective']:.6g}")
+    if f32:
+        assert min(abs(f - v) / v for v in f32) <= 1e-3, (f, f32, g["objective"])
+    else:
+        assert abs(f - g["objective"]) <= 1e-2 * g["objective"], (f, g["objective"])
 
 
 def _kkt_violation(G, B, X):

