@@ -112,7 +112,7 @@ def test_batch_of_uneven_sizes_against_oracle(h):
     import json
     import os
     from conftest import ROOT
-    from test_gpu_serve import sample_reference
+    from test_gpu_serve import BF16_SAMPLE_MEDIAN, sample_reference
     G = json.load(open(os.path.join(ROOT, "tests", "golden", "served_sample.json")))
     key = "objective" if h.precision == native.NMF_FP32 else "objective_bf16"
     batch, rows = [], []
@@ -122,12 +122,14 @@ def test_batch_of_uneven_sizes_against_oracle(h):
                           algo=row["algo"], levels=row["levels"], iters=row["iters"]))
         rows.append((row, p))
     res = h.solve_batch(batch)
-    worst = 0.0
+    errs = []
     for (st, sweeps, obj), (row, p), d in zip(res, rows, batch):
         assert st == 0
         ref_f, bar = sample_reference(row, key)
         err = abs(obj - ref_f) / ref_f
-        worst = max(worst, err)
+        errs.append(err)
         assert err <= bar, (row, obj)
         assert abs(obj - o.objective(p.M, d["V"], d["W"])) <= 1e-6 * obj
-    print(f"batch of 64 against the oracle: max rel. error {worst:.2e}")
+    if key == "objective_bf16":
+        assert float(np.median(errs)) <= BF16_SAMPLE_MEDIAN
+    print(f"batch of 64 against the oracle: max rel. error {max(errs):.2e}, median {float(np.median(errs)):.2e}")
