@@ -44,9 +44,10 @@ typedef enum {
     NMF_MU = 1,   /* Algorithm MU (Section 2.2): Lee-Seung multiplicative updates */
     NMF_ANLS = 2, /* Algorithm ANLS (Section 2.1, Appendix A.2): exact NNLS for V then W (FP64 active set) */
     NMF_ANLS_BPP = 3 /* Algorithm ANLS with its NNLS problems solved by block principal pivoting (the
-                        alternative the ANLS footnote of Section 2.1 names), FP64; rows where a passive
-                        block is numerically singular, or where pivoting does not finish within 5r
-                        exchanges, are solved by the active-set method instead */
+                        alternative the ANLS footnote of Section 2.1 names), FP64, started from the
+                        support of the incoming row; rows where a passive block is numerically
+                        singular, or where pivoting does not finish within 5r exchanges, are solved
+                        by the active-set method instead */
 } nmf_algo;
 
 /* Storage precision of M and of the GEMM operands. */

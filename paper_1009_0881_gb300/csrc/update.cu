@@ -165,12 +165,40 @@ __device__ void chol_solve(const double* L, const double* dinv, int r, const int
 // numerically singular or the cap is reached (the caller then runs the active-set
 // method); on true, x holds the solution (zero outside F).
 __device__ bool bpp_row(const double* G, int r, const double b[2], const double* bs, double tol, double* L,
-                        double* dinv, int* ord, int* inv, double* y, int lane, int max_iter, double x[2]) {
-    uint64_t F = 0;
+                        double* dinv, int* ord, int* inv, double* y, int lane, int max_iter, uint64_t warm,
+                        double x[2]) {
+    // the passive set starts from the support of the incoming row (a sweep's NNLS problems
+    // change little from one sweep to the next, so this is usually the final set)
+    uint64_t F = warm;
     double xv[2] = {0.0, 0.0};
     double g[2] = {-b[0], -b[1]};
     int nmin = r + 1, backup = 3, p = 0;
-    for (int it = 0; it < max_iter; ++it) {
+    for (int it = 0; it <= max_iter; ++it) {
+        if (it > 0 || F) {
+            xv[0] = xv[1] = 0.0;
+            if (F) {
+                if (!chol_full(G, r, F, L, dinv, ord, inv, p, lane)) return false;
+                chol_solve(L, dinv, r, ord, inv, p, F, bs, xv, y, lane);
+            }
+            // gradient outside F: g = G x - b (zero in F)
+            g[0] = -b[0];
+            g[1] = -b[1];
+            for (int l = 0; l < r; ++l) {
+                const double xl = __shfl_sync(kFull, xv[l >> 5], l & 31);
+                if (xl != 0.0) {
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const int k = lane + 32 * s;
+                        if (k < r) g[s] += G[k * r + l] * xl;
+                    }
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int k = lane + 32 * s;
+                if (k < r && ((F >> k) & 1ull)) g[s] = 0.0;
+            }
+        }
         uint64_t bad = 0;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -195,29 +223,7 @@ __device__ bool bpp_row(const double* G, int r, const double b[2], const double*
         } else {
             F ^= 1ull << (63 - __clzll((long long)bad));
         }
-        xv[0] = xv[1] = 0.0;
-        if (F) {
-            if (!chol_full(G, r, F, L, dinv, ord, inv, p, lane)) return false;
-            chol_solve(L, dinv, r, ord, inv, p, F, bs, xv, y, lane);
-        }
-        // gradient outside F: g = G x - b (zero in F)
-        g[0] = -b[0];
-        g[1] = -b[1];
-        for (int l = 0; l < r; ++l) {
-            const double xl = __shfl_sync(kFull, xv[l >> 5], l & 31);
-            if (xl != 0.0) {
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const int k = lane + 32 * s;
-                    if (k < r) g[s] += G[k * r + l] * xl;
-                }
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int k = lane + 32 * s;
-            if (k < r && ((F >> k) & 1ull)) g[s] = 0.0;
-        }
+        if (it == max_iter) break;
     }
     return false;
 }
@@ -253,12 +259,13 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
     double* dinv = L + (size_t)r * (r + 1) / 2;
     double* y = dinv + kMaxRank;
     double* bs = y + kMaxRank;
-    int* ord = reinterpret_cast<int*>(G + r * r + (size_t)kAnlsWarps * anls_warp_doubles(r)) + warp * 2 * kMaxRank;
+    const int nwarps = blockDim.x >> 5;
+    int* ord = reinterpret_cast<int*>(G + r * r + (size_t)nwarps * anls_warp_doubles(r)) + warp * 2 * kMaxRank;
     int* inv = ord + kMaxRank;
     const uint64_t all = (r == 64) ? ~0ull : ((1ull << r) - 1ull);
 
-    for (int64_t row = (int64_t)blockIdx.x * kAnlsWarps + warp; row < u.rows;
-         row += (int64_t)gridDim.x * kAnlsWarps) {
+    for (int64_t row = (int64_t)blockIdx.x * nwarps + warp; row < u.rows;
+         row += (int64_t)gridDim.x * nwarps) {
         double b[2], x[2] = {0.0, 0.0}, z[2];
         uint64_t warm = 0;
 #pragma unroll
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
         const double bmax = warp_max(fmax(fabs(b[0]), fabs(b[1])));
         const double tol = 1e-12 * fmax(1.0, bmax);
         bool capped = false;
-        if (BPP && bpp_row(G, r, b, bs, tol, L, dinv, ord, inv, y, lane, 5 * r, x)) {
+        if (BPP && bpp_row(G, r, b, bs, tol, L, dinv, ord, inv, y, lane, 5 * r, warm & all, x)) {
             // solved by block pivoting
         } else {
         uint64_t mask = 0, excluded = 0;
@@ -429,32 +436,35 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
 
 }  // namespace
 
-static size_t anls_smem_bytes(int r) {
-    return sizeof(double) * ((size_t)r * r + kAnlsWarps * anls_warp_doubles(r)) +
-           sizeof(int) * kAnlsWarps * 2 * kMaxRank;
+static size_t anls_smem_bytes(int r, int nwarps) {
+    return sizeof(double) * ((size_t)r * r + nwarps * anls_warp_doubles(r)) + sizeof(int) * nwarps * 2 * kMaxRank;
 }
 
 cudaError_t init_kernel_attributes() {
     cudaError_t e = cudaFuncSetAttribute(anls_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)anls_smem_bytes(kMaxRank));
+                                         (int)anls_smem_bytes(kMaxRank, kAnlsWarps));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(anls_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)anls_smem_bytes(kMaxRank));
+                                 (int)anls_smem_bytes(kMaxRank, kAnlsWarps));
     return e;
 }
 
 cudaError_t anls_update_launch(const UpdateArgs& u, int num_sms, int* d_status, cudaStream_t st) {
     if (u.rows <= 0) return cudaSuccess;
-    const size_t smem = anls_smem_bytes(u.r);
     if (!u.Gd) return cudaErrorInvalidValue;
     gram_reduce_f64_kernel<<<(unsigned)ceil_div((int64_t)u.r * u.r, 256), 256, 0, st>>>(u);
-    int64_t grid = ceil_div(u.rows, kAnlsWarps);
-    const int64_t cap = 8LL * num_sms;
+    // one warp per row, FP64-bound: fewer warps per CTA when the rows would not reach every
+    // SM with kAnlsWarps per CTA (the rows of a coarse level's V-step, for example)
+    int nw = kAnlsWarps;
+    while (nw > 1 && ceil_div(u.rows, nw) < num_sms) nw /= 2;
+    const size_t smem = anls_smem_bytes(u.r, nw);
+    int64_t grid = ceil_div(u.rows, nw);
+    const int64_t cap = 8LL * num_sms * (kAnlsWarps / nw);
     if (grid > cap) grid = cap;
     if (u.bpp)
-        anls_rows_kernel<true><<<(unsigned)grid, 32 * kAnlsWarps, smem, st>>>(u, d_status);
+        anls_rows_kernel<true><<<(unsigned)grid, 32 * nw, smem, st>>>(u, d_status);
     else
-        anls_rows_kernel<false><<<(unsigned)grid, 32 * kAnlsWarps, smem, st>>>(u, d_status);
+        anls_rows_kernel<false><<<(unsigned)grid, 32 * nw, smem, st>>>(u, d_status);
     return cudaGetLastError();
 }
 
