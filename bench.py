@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-rate-low", type=float, default=40.0)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-precisions", default="fp32,bf16,bf16_fp32_finish")
+    ap.add_argument("--serve-max-batches", default="16,1")
     ap.add_argument("--_oracle_sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -927,8 +929,10 @@ def serving_form(args, pool):
                       "and V, W returned to it inside that time",
            "max_batch": "requests a slot takes at once (NMF_SERVE_MAX_BATCH): 16 = one graph per combination "
                         "of shapes, 1 = the cached graph of each shape"}
-    for label, prec in (("fp32", native.NMF_FP32), ("bf16", native.NMF_BF16), ("bf16_fp32_finish", native.NMF_BF16_FP32)):
-        for mb in (16, 1):
+    precs = {"fp32": native.NMF_FP32, "bf16": native.NMF_BF16, "bf16_fp32_finish": native.NMF_BF16_FP32}
+    for label in args.serve_precisions.split(","):
+        prec = precs[label]
+        for mb in (int(x) for x in args.serve_max_batches.split(",")):
             os.environ["NMF_SERVE_MAX_BATCH"] = str(mb)
             with native.Server(0, hbm_budget_bytes=budget, slots=args.serve_slots, precision=prec) as srv:
                 # warm-up: every (problem, algorithm) once, so the slots' graphs and workspaces exist
@@ -937,7 +941,7 @@ def serving_form(args, pool):
                 warm = [srv.poll(t, -1) for t in tickets]
                 res = {"warmup_s": time.perf_counter() - t0, "warmup_ok": all(w[0] == 0 for w in warm)}
                 res["offered"] = _poisson_run(srv, pool, Mhs, args.serve_rate, args.serve_seconds, seed=7)
-                if mb == 16:
+                if mb == 16 or args.serve_max_batches == str(mb):
                     res["low_rate"] = _poisson_run(srv, pool, Mhs, args.serve_rate_low, args.serve_seconds, seed=8)
                 out[f"{label}_max_batch{mb}"] = res
     os.environ.pop("NMF_SERVE_MAX_BATCH", None)

@@ -217,8 +217,14 @@ def store(X: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 def hals_update_V_column(V: np.ndarray, A: np.ndarray, B: np.ndarray, k: int) -> None:
-    """V_:k <- max(0, (A_:k - sum_{l != k} V_:l B_lk) / B_kk), in place.
+    """Column k of V set to the exact minimiser of ||M - VW||_F over V_:k >= 0, the other
+    columns fixed (Section 2.3), in place.
 
+    With the residual R_k = M - sum_{l != k} V_:l W_l: the objective is
+    ||R_k - V_:k W_k:||^2, a separable quadratic in the entries of V_:k with curvature
+    ||W_k:||^2 = B_kk and minimiser R_k W_k:^T / B_kk; clipping it at 0 is exact
+    entrywise.  R_k W_k:^T expands to A_:k - sum_{l != k} V_:l B_lk with A = M W^T,
+    B = W W^T, so the residual is never formed.
     READING: B_kk = 0 (row k of W is zero) leaves V_:k unchanged.
     """
     if B[k, k] <= 0.0:
@@ -228,8 +234,10 @@ def hals_update_V_column(V: np.ndarray, A: np.ndarray, B: np.ndarray, k: int) ->
 
 
 def hals_update_W_row(W: np.ndarray, C: np.ndarray, D: np.ndarray, k: int) -> None:
-    """W_k: <- max(0, (C_k: - sum_{l != k} D_kl W_l:) / D_kk), in place.
-
+    """Row k of W set to the exact minimiser of ||M - VW||_F over W_k: >= 0, the other rows
+    fixed (Section 2.3), in place: by the same argument as for a column of V, the
+    minimiser is V_:k^T R_k / ||V_:k||^2 clipped at 0, with V_:k^T R_k = C_k: -
+    sum_{l != k} D_kl W_l:, C = V^T M, D = V^T V.
     READING: D_kk = 0 (column k of V is zero) leaves W_k: unchanged.
     """
     if D[k, k] <= 0.0:
@@ -239,7 +247,9 @@ def hals_update_W_row(W: np.ndarray, C: np.ndarray, D: np.ndarray, k: int) -> No
 
 
 def hals_sweep(M, V, W):
-    """One pass of the while-loop of Algorithm HALS: all columns of V, then all rows of W."""
+    """One HALS sweep (Section 2.3): block coordinate descent on ||M - VW||_F over the
+    columns of V in order 1..r (each with the columns already updated), then over the rows
+    of W in order with the new V."""
     V = np.array(V, dtype=np.float64)
     W = np.array(W, dtype=np.float64)
     A = product(M, W.T, True)
