@@ -527,11 +527,68 @@ def wcycle(Ms, grids, V, W, algo: str, L: int, K: int, level: int = 0, trace=Non
 CYCLES = {"vcycle": vcycle, "ni": nested_iteration, "fmg": full_multigrid, "wcycle": wcycle}
 
 
+# ---------------------------------------------------------------------------
+# Section 6.1: the columns of M coarsened as well (image sequences)
+# ---------------------------------------------------------------------------
+# Section 6.1 notes that when the columns of M form a smooth sequence (video frames,
+# hyperspectral bands) the multilevel strategy also applies to them.  READING: the
+# sequence is a 1-D grid of n points and is coarsened like one side of the pixel grid
+# (coarse point j on fine point 2j, ceil(n / 2) points): the restriction along it is
+# Eq. (4.1) on an n x 1 grid (weights 1, 2, 1 renormalised at the ends) and the
+# prolongation Eq. (4.2) on it.  M_{l+1} = R M_l R_n^T, W_{l+1} = W_l R_n^T and
+# W_l = W_{l+1} P_n^T, next to the pixel transfers of V; the V-cycle otherwise as
+# Algorithm V-cycle with the sweep reading of Table 1.
+
+def restrict_columns(X: np.ndarray, n: int) -> np.ndarray:
+    """X R_n^T: the columns of X (a sequence of n) restricted along the sequence."""
+    return restrict(np.asarray(X, np.float64).T, n, 1).T
+
+
+def prolong_columns(Y: np.ndarray, nc: int, n: int) -> np.ndarray:
+    """Y P_n^T: a coarse sequence of nc columns prolonged to n columns."""
+    return prolong(np.asarray(Y, np.float64).T, nc, 1, n, 1).T
+
+
+def sequence_lengths(n: int, levels: int) -> list[int]:
+    """n at levels 1 (finest) .. L."""
+    ns = [n]
+    for _ in range(levels - 1):
+        ns.append((ns[-1] + 1) // 2)
+    return ns
+
+
+def restrict_hierarchy_both(M: np.ndarray, h: int, w: int, levels: int) -> list[np.ndarray]:
+    """M at levels 1..L, restricted over the pixel grid and along the sequence."""
+    Ms = [np.asarray(M, dtype=np.float64)]
+    grids = grid_hierarchy(h, w, levels)
+    ns = sequence_lengths(M.shape[1], levels)
+    for l in range(levels - 1):
+        Ms.append(restrict_columns(restrict(Ms[-1], *grids[l]), ns[l]))
+    return Ms
+
+
+def vcycle_both(Ms, grids, ns, V, W, algo: str, L: int, K: int, level: int = 0, trace=None, hooks=None):
+    """V-cycle with V restricted over the pixel grid and W along the sequence."""
+    M = Ms[level]
+    if L == 1:
+        return smooth(M, V, W, algo, K, trace, level + 1)
+    V, W = smooth(M, V, W, algo, K // 4, trace, level + 1)
+    Vc = restrict(V, *grids[level])
+    Wc = restrict_columns(W, ns[level])
+    Vc, Wc = vcycle_both(Ms, grids, ns, Vc, Wc, algo, L - 1, K, level + 1, trace, hooks)
+    if hooks is not None:
+        hooks.append(("both", level, Vc.copy(), Wc.copy()))
+    V = prolong(Vc, *grids[level + 1], *grids[level])
+    W = prolong_columns(Wc, ns[level + 1], ns[level])
+    return smooth(M, V, W, algo, K // 2, trace, level + 1)
+
+
 def solve(M, grid_h: int, grid_w: int, V0, W0, algo: str = "hals", levels: int = 1, K: int = 100,
-          cycle: str = "vcycle", trace=None, precision: str = "fp64"):
+          cycle: str = "vcycle", trace=None, precision: str = "fp64", coarsen_columns: bool = False):
     """Multilevel NMF of M (m = grid_h * grid_w rows) from (V0, W0); returns (V, W).
 
-    precision: "fp64" (default), "fp32" or "bf16" (see PRECISION)."""
+    precision: "fp64" (default), "fp32" or "bf16" (see PRECISION).  coarsen_columns: the
+    V-cycle coarsens the columns of M as a sequence too (vcycle_both)."""
     global PRECISION
     M = np.asarray(M, dtype=np.float64)
     Ms = restrict_hierarchy(M, grid_h, grid_w, levels)
@@ -541,6 +598,10 @@ def solve(M, grid_h: int, grid_w: int, V0, W0, algo: str = "hals", levels: int =
     saved = PRECISION
     PRECISION = {"fp64": None, "fp32": "fp32", "bf16": "bf16"}[precision]
     try:
+        if coarsen_columns:
+            assert cycle == "vcycle", "column coarsening is defined for the V-cycle"
+            Ms = restrict_hierarchy_both(M, grid_h, grid_w, levels)
+            return vcycle_both(Ms, grids, sequence_lengths(M.shape[1], levels), V, W, algo, levels, K, trace=trace)
         if cycle == "vcycle":
             return vcycle(Ms, grids, V, W, algo, levels, K, trace=trace)
         return CYCLES[cycle](Ms, grids, V, W, algo, levels, K, trace=trace)

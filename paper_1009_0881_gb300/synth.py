@@ -126,6 +126,21 @@ def planted_weights(r: int, n: int, seed: int) -> np.ndarray:
     return np.where(keep, e, 0.0)
 
 
+def planted_weights_sequence(r: int, n: int, seed: int) -> np.ndarray:
+    """W0 for image sequences (video frames, spectral bands): row k is smooth along the
+    sequence, a_k exp(-(j - c_k)^2 / (2 s^2)) (1 + cos(2 pi f_k j / n + phi_k)) / 2 with
+    a_k ~ Exp(1), c_k ~ U[0, n), s = n / 6, f_k ~ U[0.5, 3], phi_k ~ U[0, 2 pi) (float64)."""
+    a = exponential(seed, STREAM_W0 + 200, r)
+    u = uniform(seed, STREAM_W0 + 300, r * 3).reshape(r, 3)
+    j = np.arange(n, dtype=np.float64)
+    s = n / 6.0
+    W0 = np.zeros((r, n))
+    for k in range(r):
+        c, f, phi = u[k, 0] * n, 0.5 + 2.5 * u[k, 1], 2.0 * np.pi * u[k, 2]
+        W0[k] = a[k] * np.exp(-((j - c) ** 2) / (2.0 * s * s)) * 0.5 * (1.0 + np.cos(2.0 * np.pi * f * j / n + phi))
+    return W0
+
+
 def initial_iterate(m: int, n: int, r: int, init_seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
     """(V, W) ~ U[0, 1], float32."""
     V = uniform(init_seed, STREAM_V_INIT, m * r).reshape(m, r).astype(np.float32)
@@ -134,17 +149,19 @@ def initial_iterate(m: int, n: int, r: int, init_seed: int = 0) -> tuple[np.ndar
 
 
 def make_problem(grid_h: int, grid_w: int, n: int, r: int, sigma: float | None = None,
-                 data_seed: int = 1, init_seed: int = 0, noise: float = 0.01) -> Problem:
+                 data_seed: int = 1, init_seed: int = 0, noise: float = 0.01, sequence: bool = False) -> Problem:
     """Draw M = max(0, V0 W0 + N) and the U[0,1] initial iterate.
 
     ``sigma`` defaults to 2 px.  ``noise`` is the noise level relative to
-    mean(V0 W0); 0 gives the exact planted factorisation M = V0 W0.
+    mean(V0 W0); 0 gives the exact planted factorisation M = V0 W0.  ``sequence``:
+    the columns form a smooth sequence (planted_weights_sequence) instead of
+    independent images.
     """
     if sigma is None:
         sigma = 2.0
     m = grid_h * grid_w
     V0 = planted_basis(grid_h, grid_w, r, sigma, data_seed)
-    W0 = planted_weights(r, n, data_seed)
+    W0 = planted_weights_sequence(r, n, data_seed) if sequence else planted_weights(r, n, data_seed)
     X = V0 @ W0
     if noise > 0:
         X = X + noise * X.mean() * gaussian(data_seed, STREAM_NOISE, m * n).reshape(m, n)
@@ -164,6 +181,14 @@ WORKLOADS = {
     "grid112x92_n400_r40": (112, 92, 400, 40, 0.04 * 92),
     # 256x256 grid, 2000 images, r = 64, sigma = 4 % of grid width
     "grid256_n2000_r64": (256, 256, 2000, 64, 0.04 * 256),
+}
+
+# Image sequences (make_problem(..., sequence=True)): (grid_h, grid_w, n, r, sigma)
+SEQUENCE_WORKLOADS = {
+    # 16x16 frames, 1024 of them, r = 10
+    "seq16_n1024_r10": (16, 16, 1024, 10, 2.0),
+    # 32x32 frames, 4096 of them, r = 16, sigma = 3 px
+    "seq32_n4096_r16": (32, 32, 4096, 16, 3.0),
 }
 
 

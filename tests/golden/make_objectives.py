@@ -47,14 +47,39 @@ CASES = [
     ("grid112x92_hals_L3_K100", "grid112x92_n400_r40", "hals", 3, 100, "vcycle"),
     ("grid256_hals_L3_K20", "grid256_n2000_r64", "hals", 3, 20, "vcycle"),
     ("grid256_hals_L3_K100", "grid256_n2000_r64", "hals", 3, 100, "vcycle"),
+    # image sequences (Section 6.1): V-cycles that coarsen the columns too ("vcycle_cols"),
+    # beside the pixel-only V-cycle and the single-level run on the same data
+    ("seq16_hals_cols_L3_K100", "seq16_n1024_r10", "hals", 3, 100, "vcycle_cols"),
+    ("seq16_mu_cols_L3_K100", "seq16_n1024_r10", "mu", 3, 100, "vcycle_cols"),
+    ("seq16_anls_cols_L3_K8", "seq16_n1024_r10", "anls", 3, 8, "vcycle_cols"),
+    ("seq16_hals_L3_K100", "seq16_n1024_r10", "hals", 3, 100, "vcycle"),
+    ("seq32_hals_cols_L3_K100", "seq32_n4096_r16", "hals", 3, 100, "vcycle_cols"),
+    ("seq32_hals_cols_L4_K100", "seq32_n4096_r16", "hals", 4, 100, "vcycle_cols"),
+    ("seq32_hals_L3_K100", "seq32_n4096_r16", "hals", 3, 100, "vcycle"),
+    ("seq32_hals_L1_K100", "seq32_n4096_r16", "hals", 1, 100, "vcycle"),
 ]
+
+
+def _problem(wl):
+    """(grid_h, grid_w, Problem) of a named workload."""
+    if wl in synth.SEQUENCE_WORKLOADS:
+        h, w, n, r, sigma = synth.SEQUENCE_WORKLOADS[wl]
+        return h, w, synth.make_problem(h, w, n, r, sigma=sigma, sequence=True)
+    h, w, n, r, sigma = synth.WORKLOADS[wl]
+    return h, w, synth.make_problem(h, w, n, r, sigma=sigma)
+
+
+def _solve(p, h, w, algo, L, K, cyc, **kw):
+    if cyc == "vcycle_cols":
+        return o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, coarsen_columns=True, **kw)
+    return o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc, **kw)
 
 
 # Cycles that start on a level with fewer pixels than the rank: their result depends on
 # rounding (oracle reading PRECISION), so the values at float32 precision are stored beside the
 # FP64 one.
 FP32_PRODUCT_CASES = {"grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100", "grid19_mu_fmg_L3_K100",
-                      "grid19_anls_fmg_L3_K8"}
+                      "grid19_anls_fmg_L3_K8", "grid19_anls_L3_K500"}
 
 
 def _fp32_value(name, threads):
@@ -72,10 +97,9 @@ def _fp32_value(name, threads):
 def _fp32_child(name):
     for nm, wl, algo, L, K, cyc in CASES:
         if nm == name:
-            h, w, n, r, sigma = synth.WORKLOADS[wl]
-            p = synth.make_problem(h, w, n, r, sigma=sigma)
+            h, w, p = _problem(wl)
             try:
-                V, W = o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc, precision="fp32")
+                V, W = _solve(p, h, w, algo, L, K, cyc, precision="fp32")
                 print(repr(o.objective(p.M.astype(np.float64), V, W)))
             except o.NNLSNotConverged:
                 print("None")
@@ -99,10 +123,9 @@ def main(only=None):
     for name, wl, algo, L, K, cyc in CASES:
         if only and name not in only:
             continue
-        h, w, n, r, sigma = synth.WORKLOADS[wl]
-        p = synth.make_problem(h, w, n, r, sigma=sigma)
+        h, w, p = _problem(wl)
         t = time.time()
-        V, W = o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc)
+        V, W = _solve(p, h, w, algo, L, K, cyc)
         f = o.objective(p.M.astype(np.float64), V, W)
         entry = {"workload": wl, "algo": algo, "levels": L, "K": K, "cycle": cyc, "objective": f,
                  "norm_M": float(np.linalg.norm(p.M.astype(np.float64)))}
@@ -115,8 +138,22 @@ def main(only=None):
         print(f"{name}: {f:.10g} ({time.time() - t:.1f} s)", flush=True)
 
 
+def add_fp32(name):
+    """Add the float32 values to a stored entry, the two summation orders run side by side
+    (for cases whose FP64 run takes hours)."""
+    from concurrent.futures import ThreadPoolExecutor
+    path = os.path.join(HERE, "objectives.json")
+    entry = json.load(open(path))[name]
+    with ThreadPoolExecutor(2) as ex:
+        entry["objective_fp32"] = list(ex.map(lambda t: _fp32_value(name, t), (1, 4)))
+    _store(path, name, entry)
+    print(f"{name}: float32 {entry['objective_fp32']}", flush=True)
+
+
 if __name__ == "__main__":
     if len(sys.argv) == 3 and sys.argv[1] == "--fp32":
         _fp32_child(sys.argv[2])
+    elif len(sys.argv) == 3 and sys.argv[1] == "--add-fp32":
+        add_fp32(sys.argv[2])
     else:
         main(sys.argv[1:] or None)

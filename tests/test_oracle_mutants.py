@@ -8,6 +8,7 @@ at least one of them must fail.  The unpatched oracle passes all of them
 import numpy as np
 import pytest
 
+import test_oracle_columns as tcol
 import test_oracle_cycles as tc
 import test_oracle_sweeps as ts
 import test_oracle_transfer as tt
@@ -200,6 +201,27 @@ def _bpp_wrong_gradient_sign(G, b, max_iter=None, info=None):
     return _bpp_variant(G, b, max_iter, info, flip_y=True)
 
 
+def _restrict_columns_zero_padded(X, n):
+    # the ends not renormalised: the missing neighbour counted as a zero
+    X = np.asarray(X, dtype=np.float64)
+    Xp = np.concatenate([np.zeros((X.shape[0], 1)), X, np.zeros((X.shape[0], 1))], axis=1)
+    return np.stack([(Xp[:, 2 * j] + 2 * Xp[:, 2 * j + 1] + Xp[:, 2 * j + 2]) / 4
+                     for j in range((n + 1) // 2)], axis=1)
+
+
+_vcycle_both = o.vcycle_both
+
+
+def _vcycle_both_w_injected(Ms, grids, ns, V, W, algo, L, K, level=0, trace=None, hooks=None):
+    # W prolonged by injection (odd columns copied from the left neighbour) instead of Eq. (4.2)
+    saved = o.prolong_columns
+    try:
+        o.prolong_columns = lambda Y, nc, n: np.asarray(Y, np.float64)[:, np.arange(n) // 2]
+        return _vcycle_both(Ms, grids, ns, V, W, algo, L, K, level, trace, hooks)
+    finally:
+        o.prolong_columns = saved
+
+
 def _table1_checks():
     return [lambda row=row: tc.test_vcycle_sweep_allocation_matches_table1(row) for row in tc._table1_rows()]
 
@@ -234,6 +256,11 @@ MUTANTS = {
     "FMG V-cycle with the initial W": ("full_multigrid", _fmg_coarse_w0, [lambda: tc.test_fmg_data_flow("hals")]),
     "BPP gradient with the wrong sign": ("nnls_bpp", _bpp_wrong_gradient_sign,
                                          [lambda s=s: ts.test_bpp_equals_support_enumeration(s) for s in range(8)]),
+    "column restriction with zero-padded ends": ("restrict_columns", _restrict_columns_zero_padded,
+                                                 [lambda: tcol.test_column_restriction_closed_form(5),
+                                                  lambda: tcol.test_pixel_operators_are_tensor_products_of_the_column_operators(4, 5)]),
+    "column V-cycle prolongs W by injection": ("vcycle_both", _vcycle_both_w_injected,
+                                               [lambda: tcol.test_column_vcycle_data_flow("hals")]),
     "W-cycle visits the coarser level once": ("wcycle", _wcycle_single_visit,
                                               [tc.test_wcycle_order_visits_the_coarser_level_twice,
                                                tc.test_wcycle_data_flow]),
