@@ -53,6 +53,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-batched-form", action="store_true")
     ap.add_argument("--no-serving-form", action="store_true")
     ap.add_argument("--no-time-to-target-table", action="store_true")
+    ap.add_argument("--no-sequence-table", action="store_true", help="skip the image-sequence (column coarsening) table")
     ap.add_argument("--no-analysis", action="store_true",
                     help="skip everything after the timed steps (for profiler launch lists)")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -467,6 +468,8 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
         out["other_algorithms"] = other_algorithms(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw)
         if not args.no_time_to_target_table:
             out["time_to_target_table"] = time_to_target_table(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw)
+        if not args.no_sequence_table:
+            out["image_sequence"] = sequence_table(h, stream, golden)
     if not args.no_precision_form:
         out["precision_form"] = precision_form(args)
     if not args.no_batched_form:
@@ -505,11 +508,12 @@ def _traffic(kernel):
     return t["bytes"] if hsh.hexdigest()[:16] == t["src"] else None
 
 
-def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, reps=3, warm=1):
+def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, reps=3, warm=1, cols=False):
     """Wall time of a V-cycle solve (device-resident inputs, CUDA events) until the finest-level
     objective first reaches (1 + 1e-3) f*, f* the FP64 oracle's final objective for the same
     (algo, L, K): the per-sweep trace locates that sweep, then solves stopped right after it
-    are timed.  None if the schedule never reaches the target."""
+    are timed.  None if the schedule never reaches the target.  cols: the V-cycle coarsens
+    the columns of M too."""
     import numpy as np
     import torch
 
@@ -519,7 +523,7 @@ def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, r
     target = (1 + 1e-3) * fstar
     Vd.copy_(V0d)
     Wd.copy_(W0d)
-    tr = h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, trace_len=sched[0])
+    tr = h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, trace_len=sched[0], coarsen_columns=cols)
     hit = np.nonzero(tr <= target)[0]
     res = {"algo": algo, "levels": L, "iters": K, "oracle_fp64": fstar, "objective_target": target,
            "final_objective_gpu": float(tr[-1]) if len(tr) else None}
@@ -536,7 +540,7 @@ def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, r
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, stop_after=stop)
+        h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, stop_after=stop, coarsen_columns=cols)
         e1.record(stream)
         e1.synchronize()
         if it >= warm:
@@ -564,6 +568,52 @@ def time_to_target_table(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw):
             slow = algo.startswith("anls")
             out[name] = time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, args.iters, fstar,
                                        reps=1 if slow else 3, warm=0 if slow else 1)
+    return out
+
+
+def sequence_table(h, stream, golden):
+    """Image sequences (32 x 32 frames, n = 4096, r = 16, HALS, K = 100): time for the
+    single-level run, the pixel-only V-cycle and the V-cycle that also coarsens the columns
+    to reach (1 + 1e-3) f*, f* the FP64 oracle's single-level objective (the weakest of the
+    three, so every run can reach it), and the wall time of the whole K = 100 solve."""
+    import torch
+
+    from paper_1009_0881_gb300 import synth
+
+    gh, gw, n, r, sigma = synth.SEQUENCE_WORKLOADS["seq32_n4096_r16"]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma, sequence=True)
+    dev = torch.device("cuda", 0)
+    Md = torch.from_numpy(p.M).to(dev)
+    V0d = torch.from_numpy(p.V).to(dev)
+    W0d = torch.from_numpy(p.W).to(dev)
+    Vd, Wd = V0d.clone(), W0d.clone()
+    fstar = golden.get("seq32_hals_L1_K100", {}).get("objective")
+    out = {"workload": "seq32_n4096_r16 (32x32 frames, n=4096, r=16, smooth along the sequence)",
+           "target": None if fstar is None else (1 + 1e-3) * fstar}
+    for name, L, cols, key in (("L1", 1, False, "seq32_hals_L1_K100"), ("L3", 3, False, "seq32_hals_L3_K100"),
+                               ("L3_cols", 3, True, "seq32_hals_cols_L3_K100")):
+        res = {"ms_to_target": None}
+        if fstar is not None:
+            t = time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, "hals", L, 100, fstar, cols=cols)
+            res = {"ms_to_target": t["ms"], "sweeps_to_target": t.get("sweeps"),
+                   "fine_sweeps_to_target": t.get("fine_sweeps")}
+        ms = []
+        for it in range(3):
+            Vd.copy_(V0d)
+            Wd.copy_(W0d)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.solve(Md, gh, gw, Vd, Wd, "hals", levels=L, iters=100, coarsen_columns=cols)
+            e1.record(stream)
+            e1.synchronize()
+            if it:
+                ms.append(e0.elapsed_time(e1))
+        f = h.error(Md, Vd, Wd)
+        fo = golden.get(key, {}).get("objective")
+        res.update(ms_K100=statistics.median(ms), objective_K100=f, oracle_fp64_K100=fo,
+                   rel_diff=None if fo is None else abs(f - fo) / fo)
+        out[name] = res
     return out
 
 

@@ -100,13 +100,21 @@ const char* nmf_last_error(nmf_handle h);
 /* Options of nmf_solve_ex.  Zero-initialise and set what is needed. */
 typedef struct {
     nmf_cycle cycle;      /* multigrid cycle (default NMF_VCYCLE) */
-    int64_t stop_after;   /* if > 0: run only the first stop_after sweeps of the schedule
-                             (the iterates are then exactly those of the full run at that point) */
+    int64_t stop_after;   /* if > 0: run only the first stop_after sweeps of the schedule and
+                             skip everything after them, transfers included (stopped in a run
+                             on the finest level, the iterates are exactly those of the full run
+                             at that point) */
     double* trace;        /* optional host array: ||M - VW||_F after each sweep at the finest level,
                              in schedule order; FP64 accumulation.  Costs one extra pass over M per
                              fine sweep. */
     int64_t trace_len;    /* capacity of trace; entries beyond it are not written */
     int64_t* trace_count; /* optional: receives the number of fine-level sweeps run */
+    int coarsen_columns;  /* nonzero: the columns of M form a sequence that varies smoothly
+                             (Section 6.1: video frames, spectral bands) and are coarsened too:
+                             level l has ceil(n_{l-1}/2) columns, M_{l+1} = R M_l R_n^T, and W
+                             moves between levels along the sequence with the operators of
+                             Eqs. (4.1) and (4.2) on an n x 1 grid, V over the pixel grid.
+                             V-cycle and the FP32 form only (NMF_EINVAL otherwise). */
 } nmf_options;
 
 /*

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "coarse.cuh"
+#include "columns.cuh"
 #include "fused.cuh"
 #include "nmf_internal.cuh"
 #include "tc_gemm.cuh"
@@ -1032,6 +1033,7 @@ cudaError_t enqueue_schedule(nmf_ctx* h, const Plan& p, const std::vector<Op>& o
     if (e != cudaSuccess) return e;
     bool gb_single = false;  // GB holds the whole of B in slab 0 (after a coarse run)
     for (int oi = 0; oi < (int)ops.size(); ++oi) {
+        if (stop_after > 0 && done >= stop_after) break;  // the rest of the schedule, transfers included
         const Op& op = ops[oi];
         const Level& f = p.lv[op.level];
         const bool watched = stop_rule && oi == last_fine;
@@ -1157,6 +1159,44 @@ int init_levels_padding(nmf_ctx* h, Plan& p) {
     return NMF_OK;
 }
 
+// The graph cached under `key` on the handle, or a new one captured from what `enqueue`
+// puts on the handle's stream (enqueue(&fine_sweeps) returns the first launch error).
+template <typename F>
+int cached_graph(nmf_ctx* h, const char* key, GraphEntry* out, F enqueue) {
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        GraphEntry ge;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue(&ge.fine_sweeps);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(h, NMF_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        size_t nn = 0;
+        e = cudaGraphGetNodes(graph, nullptr, &nn);
+        if (e == cudaSuccess && nn) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+            for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++ge.kernels;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(h, NMF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        if (h->graphs.size() >= kMaxCachedGraphs) drop_graphs(h);
+        it = h->graphs.emplace(key, ge).first;
+    }
+    *out = it->second;
+    return NMF_OK;
+}
+
+int solve_columns_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw, int r, nmf_algo algo,
+                       int L, int K, const nmf_options* opt, float* V, float* W);
+
 int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw, int r, nmf_algo algo, int L,
                int K, const nmf_options* opt, float* V, float* W) {
     if (!h) return NMF_EINVAL;
@@ -1171,6 +1211,7 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     const nmf_cycle cyc = opt ? opt->cycle : NMF_VCYCLE;
     if (cyc != NMF_VCYCLE && cyc != NMF_NESTED && cyc != NMF_FMG && cyc != NMF_WCYCLE)
         return fail(h, NMF_EINVAL, "unknown cycle");
+    if (opt && opt->coarsen_columns) return solve_columns_impl(h, M, m, n, gh, gw, r, algo, L, K, opt, V, W);
     const int64_t stop_after = opt ? opt->stop_after : 0;
     const bool trace = opt && opt->trace && opt->trace_len > 0;
     CK(cudaSetDevice(h->device));
@@ -1194,39 +1235,16 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
              r, (int)algo, L, K, (int)cyc, (long long)stop_after, (long long)(trace ? opt->trace_len : 0),
              (void*)h->ws);
     const std::vector<Op> ops = build_schedule(cyc, L, K);
-    auto it = h->graphs.find(key);
-    if (it == h->graphs.end()) {
-        GraphEntry ge;
-        cudaGraph_t graph = nullptr;
-        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    GraphEntry ge;
+    rc = cached_graph(h, key, &ge, [&](int64_t* fine) {
         cudaError_t e = enqueue_hierarchy(h, p);
-        if (e == cudaSuccess) e = enqueue_schedule(h, p, ops, algo, stop_after, trace, &ge.fine_sweeps);
-        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
-        if (e != cudaSuccess || e2 != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return fail(h, NMF_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
-        }
-        size_t nn = 0;
-        e = cudaGraphGetNodes(graph, nullptr, &nn);
-        if (e == cudaSuccess && nn) {
-            std::vector<cudaGraphNode_t> nodes(nn);
-            e = cudaGraphGetNodes(graph, nodes.data(), &nn);
-            for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
-                cudaGraphNodeType t;
-                if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++ge.kernels;
-            }
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return fail(h, NMF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-        if (h->graphs.size() >= kMaxCachedGraphs) drop_graphs(h);
-        it = h->graphs.emplace(key, ge).first;
-    }
-    const GraphEntry& ge = it->second;
-    const cudaGraphExec_t exec = ge.exec;
+        if (e == cudaSuccess) e = enqueue_schedule(h, p, ops, algo, stop_after, trace, fine);
+        return e;
+    });
+    if (rc) return rc;
     const int64_t fine_sweeps = ge.fine_sweeps;
     h->launches += ge.kernels;
-    CK(cudaGraphLaunch(exec, h->stream));
+    CK(cudaGraphLaunch(ge.exec, h->stream));
     CK(cudaMemcpyAsync(h->h_status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(h->h_flag, p.err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1245,6 +1263,171 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     CK(cudaStreamSynchronize(h->stream));
     if (opt && opt->trace_count) *opt->trace_count = fine_sweeps;
     if (*h->h_status) return fail(h, NMF_ENOCONV, "an active-set NNLS solve reached its iteration cap");
+    return NMF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle that coarsens the columns of M too (Section 6.1: the columns form a smooth
+// sequence).  Level l has the m_l pixels of the coarsened grid and n_l = ceil(n_{l-1}/2)
+// columns; each level is a single-level plan of its own (its own M, M^T, V, W^T and
+// product buffers, laid out back to back in the workspace).  The transfers between
+// levels move V over the pixel grid (Eqs. (4.1), (4.2)) and W^T along the sequence (the
+// same operators on an n_l x 1 grid); after each W transfer the B = W W^T slabs of the
+// receiving level are formed anew, since its first V-step reads them.  FP32 form.
+// ---------------------------------------------------------------------------
+struct ColumnLevels {
+    std::vector<int> gh, gw;
+    std::vector<int64_t> n;
+};
+
+cudaError_t enqueue_columns(nmf_ctx* h, std::vector<Plan>& plans, const ColumnLevels& g, const std::vector<Op>& ops,
+                            nmf_algo algo, int64_t stop_after, bool trace, int64_t* fine_sweeps) {
+    const int L = (int)plans.size();
+    int64_t done = 0, tidx = 0, launches = 0;
+    // M_{l+1} = R M_l R_n^T and its transpose (the FP32 V-step operand), once per solve
+    for (int l = 0; l + 1 < L; ++l) {
+        const Level& f = plans[l].lv[0];
+        const Level& c = plans[l + 1].lv[0];
+        cudaError_t e = restrict_both_launch(f.M, plans[l].ldm, g.gh[l], g.gw[l], g.n[l], c.M, plans[l + 1].ldm,
+                                             h->stream);
+        if (e == cudaSuccess)
+            e = copy2d_launch(c.M, plans[l + 1].ldm, c.m, g.n[l + 1], c.Mt, c.ldmt, true, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    std::vector<char> gb_single(L, 0);  // GB of a level holds the whole of B in slab 0 (after a coarse run)
+    auto gram_b = [&](int l) {
+        const Plan& q = plans[l];
+        gb_single[l] = 0;
+        return gram_tiles_launch(q.Wt, q.n, q.r, q.rp, q.wtile, q.GB, q.slab, h->stream);
+    };
+    cudaError_t e = gram_b(0);
+    if (e != cudaSuccess) return e;
+    for (const Op& op : ops) {
+        if (stop_after > 0 && done >= stop_after) break;  // the rest of the schedule, transfers included
+        const int l = op.level;
+        Plan& p = plans[l];
+        const Level& f = p.lv[0];
+        if (op.kind == OP_RESTRICT_V || op.kind == OP_PROLONG_V) {
+            Plan& c = plans[l + 1];
+            if (op.kind == OP_RESTRICT_V) {
+                e = restrict_launch(f.V, p.rp, g.gh[l], g.gw[l], p.rp, c.lv[0].V, c.rp, h->stream);
+                if (e == cudaSuccess) e = restrict_launch(p.Wt, p.rp, (int)g.n[l], 1, p.rp, c.Wt, c.rp, h->stream);
+                if (e == cudaSuccess) e = gram_b(l + 1);
+            } else {
+                e = prolong_launch(c.lv[0].V, c.rp, g.gh[l], g.gw[l], p.rp, f.V, p.rp, h->stream);
+                if (e == cudaSuccess) e = prolong_launch(c.Wt, c.rp, (int)g.n[l], 1, p.rp, p.Wt, p.rp, h->stream);
+                if (e == cudaSuccess) e = gram_b(l);
+            }
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        if (f.crun && !is_anls(algo)) {
+            int64_t cnt = op.count;
+            if (stop_after > 0) cnt = std::min<int64_t>(cnt, std::max<int64_t>(0, stop_after - done));
+            if (cnt > 0) {
+                e = enqueue_coarse_run(h, p, 0, algo, cnt);
+                if (e != cudaSuccess) return e;
+                done += cnt;
+                gb_single[l] = 1;
+            }
+            continue;
+        }
+        for (int64_t s = 0; s < op.count; ++s) {
+            if (stop_after > 0 && done >= stop_after) break;
+            e = enqueue_sweep(h, p, 0, algo, &launches, nullptr, nullptr, gb_single[l] != 0);
+            gb_single[l] = 0;
+            if (e != cudaSuccess) return e;
+            ++done;
+            if (l == 0) {
+                if (trace && tidx < p.trace_cap) {
+                    e = error_launch(f.M, p.ldm, f.V, p.Wt, p.rp, f.m, p.n, p.r, p.err_part, p.d_trace + tidx,
+                                     h->stream);
+                    if (e != cudaSuccess) return e;
+                }
+                ++tidx;
+            }
+        }
+    }
+    if (fine_sweeps) *fine_sweeps = tidx;
+    return cudaSuccess;
+}
+
+int solve_columns_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw, int r, nmf_algo algo,
+                       int L, int K, const nmf_options* opt, float* V, float* W) {
+    if (opt->cycle != NMF_VCYCLE) return fail(h, NMF_EINVAL, "column coarsening runs the V-cycle only");
+    if (h->prec != NMF_FP32) return fail(h, NMF_EINVAL, "column coarsening runs in the FP32 form only");
+    const int64_t stop_after = opt->stop_after;
+    const bool trace = opt->trace && opt->trace_len > 0;
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+    ColumnLevels g;
+    int hh = gh, ww = gw;
+    int64_t nn = n;
+    for (int l = 0; l < L; ++l) {
+        g.gh.push_back(hh);
+        g.gw.push_back(ww);
+        g.n.push_back(nn);
+        hh = (hh + 1) / 2;
+        ww = (ww + 1) / 2;
+        nn = (nn + 1) / 2;
+    }
+    std::vector<Plan> plans(L);
+    for (int l = 0; l < L; ++l) {
+        plan_dims(h, plans[l], (int64_t)g.gh[l] * g.gw[l], g.n[l], g.gh[l], g.gw[l], r, 1,
+                  l == 0 && trace ? opt->trace_len : 0);
+        plans[l].coarse_l0 = l > 0;  // coarse levels may run their sweeps in one persistent launch
+    }
+    int rc = make_plans(h, plans);
+    if (rc) return rc;
+    // coarse-level buffers: padding columns zero
+    for (int l = 1; l < L; ++l) {
+        const Plan& p = plans[l];
+        const Level& v = p.lv[0];
+        CK(cudaMemsetAsync(v.M, 0, sizeof(float) * v.m * p.ldm, h->stream));
+        CK(cudaMemsetAsync(v.Mt, 0, sizeof(float) * p.n * v.ldmt, h->stream));
+        CK(cudaMemsetAsync(v.V, 0, sizeof(float) * v.m * p.rp, h->stream));
+        CK(cudaMemsetAsync(p.Wt, 0, sizeof(float) * p.n * p.rp, h->stream));
+    }
+    Plan& p0 = plans[0];
+    rc = stage_problem(h, p0, M, V, W, true);
+    if (rc) return rc;
+    for (Plan& p : plans) {
+        CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
+    }
+    CK(cudaMemcpyAsync(h->h_bad, p0.d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+
+    char key[256];
+    snprintf(key, sizeof key, "cols:%lld:%lld:%d:%d:%d:%d:%d:%d:%lld:%lld:%p", (long long)m, (long long)n, gh, gw, r,
+             (int)algo, L, K, (long long)stop_after, (long long)(trace ? opt->trace_len : 0), (void*)h->ws);
+    const std::vector<Op> ops = build_schedule(NMF_VCYCLE, L, K);
+    GraphEntry ge;
+    rc = cached_graph(h, key, &ge,
+                      [&](int64_t* fine) { return enqueue_columns(h, plans, g, ops, algo, stop_after, trace, fine); });
+    if (rc) return rc;
+    h->launches += ge.kernels;
+    CK(cudaGraphLaunch(ge.exec, h->stream));
+    int status = 0, flag = 0;
+    for (const Plan& p : plans) {
+        CK(cudaMemcpyAsync(h->h_status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(h->h_flag, p.err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        status |= *h->h_status;
+        flag |= *h->h_flag;
+    }
+    if (*h->h_bad) return fail(h, NMF_EINVAL, "%llu negative, NaN or infinite entries in M, V0 or W0", *h->h_bad);
+    if (flag) return fail(h, NMF_ETIMEOUT, "a bounded wait for an asynchronous copy gave up");
+
+    CK(stage_out(h, p0.lv[0].V, p0.rp, m, r, V));
+    KL(1, copy2d_launch(p0.Wt, p0.rp, n, r, p0.tmp, n, true, h->stream));
+    CK(stage_out(h, p0.tmp, n, r, n, W));
+    if (trace) {
+        const int64_t cnt = std::min<int64_t>(ge.fine_sweeps, opt->trace_len);
+        if (cnt > 0) CK(cudaMemcpyAsync(opt->trace, p0.d_trace, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (opt->trace_count) *opt->trace_count = ge.fine_sweeps;
+    if (status) return fail(h, NMF_ENOCONV, "an active-set NNLS solve reached its iteration cap");
     return NMF_OK;
 }
 

@@ -68,7 +68,7 @@ class Problem(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("cycle", _I), ("stop_after", _I64), ("trace", ctypes.POINTER(ctypes.c_double)),
-                ("trace_len", _I64), ("trace_count", ctypes.POINTER(_I64))]
+                ("trace_len", _I64), ("trace_count", ctypes.POINTER(_I64)), ("coarsen_columns", _I)]
 
 
 class NMFError(RuntimeError):
@@ -166,14 +166,16 @@ class Handle:
 
     # --- entry points -------------------------------------------------------
     def solve(self, M, grid_h: int, grid_w: int, V, W, algo="hals", levels: int = 1, iters: int = 100,
-              cycle="vcycle", stop_after: int = 0, trace_len: int = 0):
-        """nmf_solve_ex: improves V (m x r) and W (r x n) in place; returns the objective trace if asked."""
+              cycle="vcycle", stop_after: int = 0, trace_len: int = 0, coarsen_columns: bool = False):
+        """nmf_solve_ex: improves V (m x r) and W (r x n) in place; returns the objective trace if asked.
+        coarsen_columns: the columns of M are a smooth sequence, coarsened by the V-cycle too."""
         _check_f32(M, V, W)
         m, n = M.shape
         r = V.shape[1]
         opt = Options()
         opt.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
         opt.stop_after = stop_after
+        opt.coarsen_columns = 1 if coarsen_columns else 0
         trace = None
         count = _I64(0)
         if trace_len > 0:
