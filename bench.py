@@ -837,9 +837,33 @@ def _request(p, Md, algo, V=None, W=None, iters=None):
                 iters=(iters or BATCH_ITERS)[algo], rel_tol=BATCH_TOL)
 
 
+def _batch_flops(pool, res, L, K):
+    """Algorithmic flops of a solved batch (Appendix A.1 per sweep, 4 m_l n r + 4 (m_l + n) r^2)
+    from each problem's schedule, its finest-level post-smoothing cut to the sweeps it ran."""
+    import numpy as np
+
+    from paper_1009_0881_gb300 import native
+
+    total = 0.0
+    for p, (_, sweeps, _) in zip(pool, res):
+        m, n = p.M.shape
+        r = p.V.shape[1]
+        per_level = native.schedule("vcycle", L, K)
+        full = int(np.sum(per_level))
+        gh, gw = p.grid_h, p.grid_w
+        for lvl, cnt in enumerate(per_level):
+            ml = gh * gw
+            if lvl == 0:
+                cnt = cnt - (full - sweeps)
+            total += cnt * (4.0 * ml * n * r + 4.0 * (ml + n) * r * r)
+            gh, gw = (gh + 1) // 2, (gw + 1) // 2
+    return total
+
+
 def batched_form(args, pool, reps=3):
     """All 64 problems in one nmf_solve_batch (one CUDA graph of concurrent branches), FP32 and
-    BF16, next to the plain FP32 path solving them one request at a time."""
+    BF16, and in one nmf_solve_grouped (every half-sweep one persistent launch over the tiles
+    of all 64; FP32), next to the plain FP32 path solving them one request at a time."""
     import torch
 
     from paper_1009_0881_gb300 import native
@@ -860,6 +884,7 @@ def batched_form(args, pool, reps=3):
     out = {"problems": len(pool), "levels": BATCH_LEVELS, "iters_cap": BATCH_ITERS["hals"], "rel_tol": BATCH_TOL,
            "algo": "hals", "flops_per_batch_note": "sum over problems of the Appendix A.1 sweep cost"}
     for label, prec, batched in (("batched_fp32", native.NMF_FP32, True), ("batched_bf16", native.NMF_BF16, True),
+                                 ("grouped_fp32", native.NMF_FP32, "grouped"),
                                  ("sequential_plain_fp32", native.NMF_FP32, False)):
         with native.Handle(0, precision=prec) as hh:
             hh.set_stream(stream.cuda_stream)
@@ -869,7 +894,9 @@ def batched_form(args, pool, reps=3):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                if batched:
+                if batched == "grouped":
+                    res = hh.solve_batch(reqs, grouped=True)
+                elif batched:
                     res = hh.solve_batch(reqs)
                 else:
                     res = [hh.solve_batch([d])[0] for d in reqs]
@@ -879,13 +906,17 @@ def batched_form(args, pool, reps=3):
                     ms.append(e0.elapsed_time(e1))
             t = statistics.median(ms)
             sweeps = sum(x[1] for x in res)
+            fl = _batch_flops(pool, res, BATCH_LEVELS, BATCH_ITERS["hals"])
             out[label] = {"ms_per_batch": t, "solves_per_s": len(pool) / (t / 1e3), "sweeps": sweeps,
                           "sweeps_per_s": sweeps / (t / 1e3), "all_ok": all(x[0] == 0 for x in res),
-                          "objective_sum": sum(x[2] for x in res)}
+                          "objective_sum": sum(x[2] for x in res), "algorithmic_tflop": fl / 1e12,
+                          "tflop_per_s": fl / (t / 1e3) / 1e12}
     out["speedup_batched_bf16_vs_sequential_fp32"] = (out["sequential_plain_fp32"]["ms_per_batch"]
                                                       / out["batched_bf16"]["ms_per_batch"])
     out["speedup_batched_fp32_vs_sequential_fp32"] = (out["sequential_plain_fp32"]["ms_per_batch"]
                                                       / out["batched_fp32"]["ms_per_batch"])
+    out["speedup_grouped_fp32_vs_sequential_fp32"] = (out["sequential_plain_fp32"]["ms_per_batch"]
+                                                      / out["grouped_fp32"]["ms_per_batch"])
     del Mds, V0s, W0s, Vs, Ws
     torch.cuda.empty_cache()
     return out

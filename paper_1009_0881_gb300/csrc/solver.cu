@@ -21,6 +21,7 @@
 #include "coarse.cuh"
 #include "columns.cuh"
 #include "fused.cuh"
+#include "grouped.cuh"
 #include "nmf_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -177,6 +178,8 @@ struct Plan {
     float* cred = nullptr;    // coarse runs: reduced products of a V-step
     unsigned* cbar = nullptr; // coarse runs: grid-barrier counter
     bool coarse_l0 = false;   // let level 0 use the coarse-run kernel too (nmf_profile_coarse)
+    bool fixed_tiles = false; // keep the tile heights set by the caller (no tuning)
+    float* Gred = nullptr;    // grouped solves: reduced Gram matrix of the next half-sweep (r x rp)
     int* err_flag = nullptr;
     double* err_part = nullptr;
     double* Gd = nullptr;  // ANLS: FP64 Gram matrix (r x r)
@@ -373,6 +376,7 @@ void layout(Plan& p, Bump& b, int num_sms) {
         p.cred = b.take<float>((size_t)max_cred);
         p.cbar = b.take<unsigned>(1);
     }
+    p.Gred = b.take<float>((size_t)p.slab);
     p.PA = b.take<float>((size_t)(p.lv[0].m * rp));
     p.PC = b.take<float>((size_t)(n * rp));
     p.err_flag = b.take<int>(1);
@@ -624,7 +628,7 @@ bool tune_enabled() {
 
 // Tiles already tuned for this shape (plan_dims applies them).
 void apply_tuned(nmf_ctx* h, Plan& p) {
-    if (p.bf16 || !tune_enabled() || p.max_ctas < h->num_sms) return;
+    if (p.bf16 || p.fixed_tiles || !tune_enabled() || p.max_ctas < h->num_sms) return;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key('W', h->device, p.n, p.lv[0].m, p.r));
     if (it != g_tune.end()) p.wtile = it->second;
@@ -664,7 +668,7 @@ int plan_half_sweeps(nmf_ctx* h, Plan& p);
 
 // Time the candidates of every untuned half-sweep of p and record the fastest.
 int tune_plan(nmf_ctx* h, Plan& p) {
-    if (p.bf16 || !tune_enabled() || p.max_ctas < h->num_sms) return NMF_OK;
+    if (p.bf16 || p.fixed_tiles || !tune_enabled() || p.max_ctas < h->num_sms) return NMF_OK;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int cands[3] = {64, 32, 16};
     auto pick = [&](char which, int64_t rows, int current, auto set, auto launch_of) -> int {
@@ -718,16 +722,26 @@ int tune_plan(nmf_ctx* h, Plan& p) {
 }
 
 
-// Plans of several problems laid out back to back in the handle's workspace.
-int make_plans(nmf_ctx* h, std::vector<Plan>& plans) {
+// Plans of several problems laid out back to back in the handle's workspace, followed by
+// `extra` bytes for the caller (at *extra_out, 256-byte aligned).
+int make_plans(nmf_ctx* h, std::vector<Plan>& plans, size_t extra = 0, char** extra_out = nullptr) {
     Bump dry;
     for (Plan& p : plans) layout(p, dry, h->num_sms);
+    if (extra) dry.take<char>(extra);
     int rc = ensure_workspace(h, dry.off);
     if (rc) return rc;
     Bump real;
     real.dry = false;
     real.base = h->ws;
     real.cap = h->ws_cap;
+    if (extra) {
+        // the caller's bytes go after the plans: lay the plans out first
+        Bump probe;
+        for (Plan& p : plans) layout(p, probe, h->num_sms);
+        real.off = probe.off;
+        *extra_out = real.take<char>(extra);
+        real.off = 0;
+    }
     for (Plan& p : plans) {
         layout(p, real, h->num_sms);
         rc = plan_half_sweeps(h, p);
@@ -1447,8 +1461,10 @@ int ensure_branches(nmf_ctx* h, int n) {
     return NMF_OK;
 }
 
-int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
-    if (!h) return NMF_EINVAL;
+int batch_results(nmf_ctx* h, nmf_problem* probs, const std::vector<Plan>& plans, int count);
+
+// Checks of a batch's problem records shared by the batched and grouped forms.
+int check_problems(nmf_ctx* h, const nmf_problem* probs, int count) {
     if (!probs || count < 1) return fail(h, NMF_EINVAL, "empty batch");
     for (int i = 0; i < count; ++i) {
         const nmf_problem& q = probs[i];
@@ -1463,6 +1479,13 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
         if (q.cycle != NMF_VCYCLE && q.cycle != NMF_NESTED && q.cycle != NMF_FMG && q.cycle != NMF_WCYCLE)
             return fail(h, NMF_EINVAL, "problem %d: unknown cycle", i);
     }
+    return NMF_OK;
+}
+
+int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
+    if (!h) return NMF_EINVAL;
+    int rc0 = check_problems(h, probs, count);
+    if (rc0) return rc0;
     CK(cudaSetDevice(h->device));
     h->launches = 0;
     std::vector<Plan> plans(count);
@@ -1548,8 +1571,11 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
     h->launches += it->second.kernels;
     CK(cudaGraphLaunch(it->second.exec, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    return batch_results(h, probs, plans, count);
+}
 
-    // per-problem results and statuses
+// Per-problem results and statuses of a batched or grouped solve (after its graph ran).
+int batch_results(nmf_ctx* h, nmf_problem* probs, const std::vector<Plan>& plans, int count) {
     int first_bad = NMF_OK;
     for (int i = 0; i < count; ++i) {
         nmf_problem& q = probs[i];
@@ -1594,6 +1620,206 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
     return first_bad;
 }
 
+// ---------------------------------------------------------------------------
+// Grouped form of a batch: every half-sweep of the schedule the problems share is one
+// persistent launch over the 64-row tiles of all of them (grouped.cu), after one launch
+// that reduces each problem's Gram slabs; transfers and the stopping rule's objective run
+// per problem between them.  FP32 form, HALS and MU.  A problem's result does not depend
+// on the rest of the group (every sum has an order fixed by the problem alone).
+// ---------------------------------------------------------------------------
+int grouped_impl(nmf_ctx* h, nmf_problem* probs, int count) {
+    if (!h) return NMF_EINVAL;
+    int rc = check_problems(h, probs, count);
+    if (rc) return rc;
+    if (h->prec != NMF_FP32) return fail(h, NMF_EINVAL, "the grouped form runs in the FP32 form only");
+    const nmf_problem& q0 = probs[0];
+    for (int i = 0; i < count; ++i) {
+        const nmf_problem& q = probs[i];
+        if (q.algo != NMF_HALS && q.algo != NMF_MU)
+            return fail(h, NMF_EINVAL, "problem %d: the grouped form runs HALS and MU only", i);
+        if (q.levels != q0.levels || q.iters != q0.iters || q.cycle != q0.cycle)
+            return fail(h, NMF_EINVAL, "problem %d: the grouped form needs one cycle, level count and budget", i);
+    }
+    CK(cudaSetDevice(h->device));
+    h->launches = 0;
+    const int L = q0.levels;
+    std::vector<Plan> plans(count);
+    for (int i = 0; i < count; ++i) {
+        Plan& p = plans[i];
+        p.fixed_tiles = true;
+        plan_dims(h, p, probs[i].m, probs[i].n, probs[i].grid_h, probs[i].grid_w, probs[i].r, L, 0);
+        p.wtile = kGroupTile;
+        for (int l = 0; l < L; ++l) p.lv[l].vtile = kGroupTile;
+    }
+    const std::vector<Op> ops = build_schedule(q0.cycle, L, q0.iters);
+    int64_t nsweeps = 0;
+    int last_fine = -1;
+    for (int k = 0; k < (int)ops.size(); ++k)
+        if (ops[k].kind == OP_SWEEPS) {
+            nsweeps += ops[k].count;
+            if (ops[k].level == 0) last_fine = k;
+        }
+    const int64_t nphase = 2 * nsweeps;
+    // work items of each (level, half), the most expensive tiles first; descriptor of
+    // problem i at (level l, half hf) at index (2 l + hf) count + i
+    const int ngroups = 2 * L;
+    std::vector<GroupItem> items;
+    std::vector<int64_t> item_off(ngroups + 1, 0);
+    for (int g = 0; g < ngroups; ++g) {
+        const int l = g / 2, hf = g % 2;
+        std::vector<std::pair<int64_t, GroupItem>> v;
+        for (int i = 0; i < count; ++i) {
+            int64_t gh = probs[i].grid_h, gw = probs[i].grid_w;
+            for (int k = 0; k < l; ++k) gh = (gh + 1) / 2, gw = (gw + 1) / 2;
+            const int64_t ml = gh * gw, n = probs[i].n;
+            const int64_t tiles = ceil_div(hf == 0 ? ml : n, kGroupTile);
+            const int64_t cost = (hf == 0 ? n : ml) * pick_br((int)round_up(probs[i].r, 4));
+            for (int64_t t = 0; t < tiles; ++t) v.push_back({cost, GroupItem{g * count + i, (int)t}});
+        }
+        std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+        for (auto& e : v) items.push_back(e.second);
+        item_off[g + 1] = (int64_t)items.size();
+    }
+    int nconv = 0;
+    for (int i = 0; i < count; ++i) nconv += probs[i].rel_tol > 0.0 ? 1 : 0;
+    const size_t ndesc = (size_t)ngroups * count;
+    const size_t extra = sizeof(GroupDesc) * ndesc + sizeof(GramJob) * ndesc + sizeof(GroupItem) * items.size() +
+                         sizeof(int) * (size_t)nphase + sizeof(ConvJob) * (size_t)std::max(1, nconv) + 6 * 256;
+    char* xbase = nullptr;
+    rc = make_plans(h, plans, extra, &xbase);
+    if (rc) return rc;
+    Bump xb;
+    xb.dry = false;
+    xb.base = xbase;
+    xb.cap = extra;
+    GroupDesc* d_desc = xb.take<GroupDesc>(ndesc);
+    GramJob* d_jobs = xb.take<GramJob>(ndesc);
+    GroupItem* d_items = xb.take<GroupItem>(items.size());
+    int* d_counters = xb.take<int>((size_t)nphase);
+    ConvJob* d_conv = xb.take<ConvJob>((size_t)std::max(1, nconv));
+
+    for (int i = 0; i < count; ++i) {
+        Plan& p = plans[i];
+        rc = init_levels_padding(h, p);
+        if (rc) return rc;
+        rc = stage_problem(h, p, probs[i].M, probs[i].V, probs[i].W, true);
+        if (rc) return rc;
+        CK(cudaMemsetAsync(p.d_status, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(p.err_flag, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(p.conv_state, 0, 3 * sizeof(double), h->stream));
+        CK(cudaMemsetAsync(p.conv_flag, 0, sizeof(int), h->stream));
+        CK(cudaMemsetAsync(p.conv_count, 0, sizeof(long long), h->stream));
+    }
+    // descriptors, Gram jobs, work items and stopping-rule jobs (rewritten every call: the
+    // workspace may have served other solves since the graph was captured)
+    std::vector<GroupDesc> hd(ndesc);
+    std::vector<GramJob> hj(ndesc);
+    std::vector<ConvJob> hc;
+    int max_f4 = 1;
+    for (int i = 0; i < count; ++i) {
+        Plan& p = plans[i];
+        const bool rule = probs[i].rel_tol > 0.0;
+        const int mode = probs[i].algo == NMF_HALS ? kModeHals : kModeMu;
+        max_f4 = std::max(max_f4, p.r * p.rp / 4);
+        for (int l = 0; l < L; ++l) {
+            const Level& v = p.lv[l];
+            for (int hf = 0; hf < 2; ++hf) {
+                const size_t idx = (size_t)(2 * l + hf) * count + i;
+                GroupDesc& d = hd[idx];
+                const HalfSweepLaunch& hs = hf == 0 ? v.hsV : v.hsW;
+                d.tmX = hs.tmX;
+                d.tmY = hs.tmY;
+                d.F = hf == 0 ? v.V : p.Wt;
+                d.G = p.Gred;
+                d.Gout = hf == 0 ? p.GD : p.GB;
+                d.skip = rule ? p.conv_flag : nullptr;
+                d.obj_part = (rule && hf == 1 && l == 0) ? p.obj_part : nullptr;
+                d.err_flag = p.err_flag;
+                d.K = hf == 0 ? p.n : v.m;
+                d.gout_stride = p.slab;
+                d.Na = (int)(hf == 0 ? v.m : p.n);
+                d.r = p.r;
+                d.rp = p.rp;
+                d.br = p.br;
+                d.mode = mode;
+                GramJob& j = hj[idx];
+                j.slabs = hf == 0 ? p.GB : p.GD;
+                j.stride = p.slab;
+                j.count = hf == 0 ? p.gb_count : v.gd_count;
+                j.f4 = p.r * p.rp / 4;
+                j.out = p.Gred;
+                j.skip = d.skip;
+            }
+        }
+        if (rule)
+            hc.push_back(ConvJob{p.obj_part, p.gb_count, p.mnorm, p.conv_state, p.conv_flag, probs[i].rel_tol,
+                                 p.conv_count});
+    }
+    CK(cudaMemcpyAsync(d_desc, hd.data(), sizeof(GroupDesc) * ndesc, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d_jobs, hj.data(), sizeof(GramJob) * ndesc, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d_items, items.data(), sizeof(GroupItem) * items.size(), cudaMemcpyHostToDevice, h->stream));
+    if (nconv) CK(cudaMemcpyAsync(d_conv, hc.data(), sizeof(ConvJob) * nconv, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope below
+
+    std::string key = "grouped";
+    char buf[160];
+    for (int i = 0; i < count; ++i) {
+        const nmf_problem& q = probs[i];
+        snprintf(buf, sizeof buf, ":%lld,%lld,%d,%d,%d,%d,%.3g", (long long)q.m, (long long)q.n, q.grid_h, q.grid_w,
+                 q.r, (int)q.algo, q.rel_tol);
+        key += buf;
+    }
+    snprintf(buf, sizeof buf, ":%d,%d,%d:%p", L, q0.iters, (int)q0.cycle, (void*)h->ws);
+    key += buf;
+    GraphEntry ge;
+    rc = cached_graph(h, key.c_str(), &ge, [&](int64_t*) {
+        cudaError_t e = cudaMemsetAsync(d_counters, 0, sizeof(int) * (size_t)nphase, h->stream);
+        for (int i = 0; i < count && e == cudaSuccess; ++i) {
+            const Plan& p = plans[i];
+            e = enqueue_hierarchy(h, p);
+            if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream);
+            if (e == cudaSuccess && probs[i].rel_tol > 0.0)
+                e = norm_launch(p.lv[0].M, p.ldm, p.lv[0].m, p.n, p.err_part, error_partials_needed(p.lv[0].m, p.n),
+                                p.mnorm, h->stream);
+        }
+        int64_t ph = 0;
+        for (int k = 0; k < (int)ops.size() && e == cudaSuccess; ++k) {
+            const Op& op = ops[k];
+            if (op.kind == OP_RESTRICT_V || op.kind == OP_PROLONG_V) {
+                for (int i = 0; i < count && e == cudaSuccess; ++i) {
+                    const Plan& p = plans[i];
+                    const Level& f = p.lv[op.level];
+                    const Level& c = p.lv[op.level + 1];
+                    e = op.kind == OP_RESTRICT_V ? restrict_launch(f.V, p.rp, f.h, f.w, p.rp, c.V, p.rp, h->stream)
+                                                 : prolong_launch(c.V, p.rp, f.h, f.w, p.rp, f.V, p.rp, h->stream);
+                }
+                continue;
+            }
+            for (int64_t sw = 0; sw < op.count && e == cudaSuccess; ++sw) {
+                for (int hf = 0; hf < 2 && e == cudaSuccess; ++hf) {
+                    const int g = 2 * op.level + hf;
+                    e = grouped_gram_launch(d_jobs + (size_t)g * count, count, max_f4, h->stream);
+                    if (e == cudaSuccess)
+                        e = grouped_half_sweep_launch(d_desc, d_items + item_off[g], (int)(item_off[g + 1] - item_off[g]),
+                                                      d_counters + ph++, h->num_sms, h->stream);
+                }
+                if (e == cudaSuccess && k == last_fine && nconv) e = grouped_converge_launch(d_conv, nconv, h->stream);
+            }
+        }
+        for (int i = 0; i < count && e == cudaSuccess; ++i) {
+            const Plan& p = plans[i];
+            e = error_launch(p.lv[0].M, p.ldm, p.lv[0].V, p.Wt, p.rp, p.m, p.n, p.r, p.err_part, p.conv_state + 2,
+                             h->stream);
+        }
+        return e;
+    });
+    if (rc) return rc;
+    h->launches += ge.kernels;
+    CK(cudaGraphLaunch(ge.exec, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return batch_results(h, probs, plans, count);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1627,7 +1853,8 @@ int nmf_create(nmf_handle* out, int device, size_t hbm_budget_bytes, nmf_precisi
     }
     h->stream = h->own_stream;
     if (init_kernel_attributes() != cudaSuccess || tma_init() != cudaSuccess || half_sweep_init() != cudaSuccess ||
-        tc_gemm_init() != cudaSuccess || rows_update_init() != cudaSuccess || coarse_init() != cudaSuccess) {
+        tc_gemm_init() != cudaSuccess || rows_update_init() != cudaSuccess || coarse_init() != cudaSuccess ||
+        grouped_init() != cudaSuccess) {
         cudaGetLastError();
         nmf_destroy(h);
         return NMF_ECUDA;
@@ -1682,6 +1909,8 @@ int nmf_solve_ex(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h,
 }
 
 int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count) { return batch_impl(h, probs, count); }
+
+int nmf_solve_grouped(nmf_handle h, nmf_problem* probs, int count) { return grouped_impl(h, probs, count); }
 
 int64_t nmf_workspace_bytes(nmf_handle h, const nmf_problem* probs, int count) {
     if (!h || !probs || count < 1) return NMF_EINVAL;

@@ -48,6 +48,7 @@ SIGNATURES = [
     ("nmf_profile_coarse", _I, [_P, _P, _I64, _I64, _I, _I, _P, _P, _I, ctypes.POINTER(ctypes.c_float)]),
     ("nmf_error_noalloc", _I, [_P, _P, _P, _I64, _I64, _I, _P, ctypes.POINTER(ctypes.c_double)]),
     ("nmf_solve_batch", _I, [_P, _P, _I]),
+    ("nmf_solve_grouped", _I, [_P, _P, _I]),
     ("nmf_workspace_bytes", _I64, [_P, _P, _I]),
     ("nmf_release_workspace", _I, [_P]),
     ("nmf_server_create", _I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I, _I]),
@@ -190,14 +191,15 @@ class Handle:
             return trace[: min(count.value, trace_len)]
         return None
 
-    def solve_batch(self, problems):
-        """nmf_solve_batch.  `problems`: list of dicts with keys M, grid_h, grid_w, V, W and optional
-        algo, levels, iters, cycle, rel_tol.  V and W are improved in place; returns a list of
-        (status, sweeps_run, objective)."""
+    def solve_batch(self, problems, grouped: bool = False):
+        """nmf_solve_batch (grouped=True: nmf_solve_grouped).  `problems`: list of dicts with keys
+        M, grid_h, grid_w, V, W and optional algo, levels, iters, cycle, rel_tol.  V and W are
+        improved in place; returns a list of (status, sweeps_run, objective)."""
         arr = (Problem * len(problems))()
         for q, d in zip(arr, problems):
             fill_problem(q, d)
-        rc = self.lib.nmf_solve_batch(self.h, ctypes.cast(arr, _P), len(problems))
+        fn = self.lib.nmf_solve_grouped if grouped else self.lib.nmf_solve_batch
+        rc = fn(self.h, ctypes.cast(arr, _P), len(problems))
         out = [(q.status, q.sweeps_run, q.objective) for q in arr]
         if rc != 0 and all(s == 0 for s, _, _ in out):
             self._rc(rc)
