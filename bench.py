@@ -568,14 +568,21 @@ def time_to_target_table(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw):
             slow = algo.startswith("anls")
             out[name] = time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, args.iters, fstar,
                                        reps=1 if slow else 3, warm=0 if slow else 1)
+            f1 = golden.get(f"grid19_{'anls' if algo == 'anls_bpp' else algo}_L1_K{args.iters}", {}).get("objective")
+            if L > 1 and f1 is not None:
+                # the same run against the single-level run's target (one objective for both)
+                t1 = time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, args.iters, f1,
+                                    reps=1 if slow else 3, warm=0 if slow else 1)
+                out[name]["single_level_target"] = {k: t1.get(k) for k in ("objective_target", "ms", "sweeps",
+                                                                            "fine_sweeps", "reached")}
     return out
 
 
 def sequence_table(h, stream, golden):
-    """Image sequences (32 x 32 frames, n = 4096, r = 16, HALS, K = 100): time for the
-    single-level run, the pixel-only V-cycle and the V-cycle that also coarsens the columns
-    to reach (1 + 1e-3) f*, f* the FP64 oracle's single-level objective (the weakest of the
-    three, so every run can reach it), and the wall time of the whole K = 100 solve."""
+    """Image sequences (32 x 32 frames, n = 4096, r = 16): time for the single-level run, the
+    pixel-only V-cycle and the V-cycle that also coarsens the columns to reach (1 + 1e-3) f*,
+    f* the FP64 oracle's single-level objective (the weakest of the three, so every run can
+    reach it), and the wall time of the whole solve; HALS with K = 100 and ANLS with K = 20."""
     import torch
 
     from paper_1009_0881_gb300 import synth
@@ -587,33 +594,35 @@ def sequence_table(h, stream, golden):
     V0d = torch.from_numpy(p.V).to(dev)
     W0d = torch.from_numpy(p.W).to(dev)
     Vd, Wd = V0d.clone(), W0d.clone()
-    fstar = golden.get("seq32_hals_L1_K100", {}).get("objective")
-    out = {"workload": "seq32_n4096_r16 (32x32 frames, n=4096, r=16, smooth along the sequence)",
-           "target": None if fstar is None else (1 + 1e-3) * fstar}
-    for name, L, cols, key in (("L1", 1, False, "seq32_hals_L1_K100"), ("L3", 3, False, "seq32_hals_L3_K100"),
-                               ("L3_cols", 3, True, "seq32_hals_cols_L3_K100")):
-        res = {"ms_to_target": None}
-        if fstar is not None:
-            t = time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, "hals", L, 100, fstar, cols=cols)
-            res = {"ms_to_target": t["ms"], "sweeps_to_target": t.get("sweeps"),
-                   "fine_sweeps_to_target": t.get("fine_sweeps")}
-        ms = []
-        for it in range(3):
-            Vd.copy_(V0d)
-            Wd.copy_(W0d)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            h.solve(Md, gh, gw, Vd, Wd, "hals", levels=L, iters=100, coarsen_columns=cols)
-            e1.record(stream)
-            e1.synchronize()
-            if it:
-                ms.append(e0.elapsed_time(e1))
-        f = h.error(Md, Vd, Wd)
-        fo = golden.get(key, {}).get("objective")
-        res.update(ms_K100=statistics.median(ms), objective_K100=f, oracle_fp64_K100=fo,
-                   rel_diff=None if fo is None else abs(f - fo) / fo)
-        out[name] = res
+    out = {"workload": "seq32_n4096_r16 (32x32 frames, n=4096, r=16, smooth along the sequence)"}
+    for algo, K in (("hals", 100), ("anls", 20)):
+        fstar = golden.get(f"seq32_{algo}_L1_K{K}", {}).get("objective")
+        tab = {"K": K, "target": None if fstar is None else (1 + 1e-3) * fstar}
+        for name, L, cols in (("L1", 1, False), ("L3", 3, False), ("L3_cols", 3, True)):
+            key = f"seq32_{algo}_{'cols_' if cols else ''}L{L}_K{K}"
+            res = {"ms_to_target": None}
+            if fstar is not None:
+                t = time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, cols=cols)
+                res = {"ms_to_target": t["ms"], "sweeps_to_target": t.get("sweeps"),
+                       "fine_sweeps_to_target": t.get("fine_sweeps")}
+            ms = []
+            for it in range(3):
+                Vd.copy_(V0d)
+                Wd.copy_(W0d)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, coarsen_columns=cols)
+                e1.record(stream)
+                e1.synchronize()
+                if it:
+                    ms.append(e0.elapsed_time(e1))
+            f = h.error(Md, Vd, Wd)
+            fo = golden.get(key, {}).get("objective")
+            res.update(ms_whole_solve=statistics.median(ms), objective=f, oracle_fp64=fo,
+                       rel_diff=None if fo is None else abs(f - fo) / fo)
+            tab[name] = res
+        out[algo] = tab
     return out
 
 

@@ -57,6 +57,10 @@ CASES = [
     ("seq32_hals_cols_L4_K100", "seq32_n4096_r16", "hals", 4, 100, "vcycle_cols"),
     ("seq32_hals_L3_K100", "seq32_n4096_r16", "hals", 3, 100, "vcycle"),
     ("seq32_hals_L1_K100", "seq32_n4096_r16", "hals", 1, 100, "vcycle"),
+    # ANLS on the sequence: the W-step's n rows shrink with the columns (Section 6.1)
+    ("seq32_anls_L1_K20", "seq32_n4096_r16", "anls", 1, 20, "vcycle"),
+    ("seq32_anls_L3_K20", "seq32_n4096_r16", "anls", 3, 20, "vcycle"),
+    ("seq32_anls_cols_L3_K20", "seq32_n4096_r16", "anls", 3, 20, "vcycle_cols"),
 ]
 
 
