@@ -74,6 +74,8 @@ struct UpdateArgs {
     double* Gd;        // ANLS: r x r scratch receiving the FP64 sum of the Gram partials
     int max_outer;     // ANLS: cap on the variables added per row (< 0: 3r, the default)
     int bpp;           // ANLS: 1 = block principal pivoting first (active set where it cannot finish)
+    int rank_cap;      // ANLS: when the other factor has fewer rows than r, their number (G has at most
+                       // that rank, and a passive set of that size already fits P_i exactly); else 0
     const int* skip;   // optional: when *skip != 0 the launch does nothing (converged problem)
 };
 

@@ -849,6 +849,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.Gd = p.Gd;
         u.max_outer = h->nnls_cap;
         u.bpp = algo == NMF_ANLS_BPP;
+        u.rank_cap = p.n < p.r ? (int)p.n : 0;  // G = W W^T
         u.skip = skip;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e == cudaSuccess) e = gram_tiles_launch(v.V, v.m, p.r, p.rp, v.vtile, p.GD, p.slab, h->stream, skip);
@@ -879,6 +880,7 @@ cudaError_t enqueue_sweep(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, int64
         u.Gd = p.Gd;
         u.max_outer = h->nnls_cap;
         u.bpp = algo == NMF_ANLS_BPP;
+        u.rank_cap = v.m < p.r ? (int)v.m : 0;  // G = V^T V
         u.skip = skip;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e == cudaSuccess) e = gram_tiles_launch(p.Wt, p.n, p.r, p.rp, p.wtile, p.GB, p.slab, h->stream, skip);
@@ -985,6 +987,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
         u.Gd = p.Gd;
         u.max_outer = h->nnls_cap;
         u.bpp = algo == NMF_ANLS_BPP;
+        u.rank_cap = p.n < p.r ? (int)p.n : 0;  // G = W W^T
         u.skip = skip;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e != cudaSuccess) return e;
@@ -1019,6 +1022,7 @@ cudaError_t enqueue_sweep_bf16(nmf_ctx* h, const Plan& p, int l, nmf_algo algo, 
         u.Gd = p.Gd;
         u.max_outer = h->nnls_cap;
         u.bpp = algo == NMF_ANLS_BPP;
+        u.rank_cap = v.m < p.r ? (int)v.m : 0;  // G = V^T V
         u.skip = skip;
         e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
         if (e != cudaSuccess) return e;
@@ -2168,6 +2172,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
                     u.Gd = p.Gd;
                     u.max_outer = h->nnls_cap;
                     u.bpp = algo == NMF_ANLS_BPP;
+                    u.rank_cap = vstep ? (p.n < p.r ? (int)p.n : 0) : (v.m < p.r ? (int)v.m : 0);
                     u.skip = nullptr;
                     e = anls_update_launch(u, h->num_sms, p.d_status, h->stream);
                     if (e == cudaSuccess)

@@ -325,6 +325,9 @@ __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const Update
         double w[2] = {0.0, 0.0};
         bool have_w = false;
         for (int outer = 0;; ++outer) {
+            // a passive set as large as G's rank bound spans the other factor's rows: the
+            // residual of the row is zero and x is optimal (the duals left are rounding)
+            if (u.rank_cap > 0 && p >= u.rank_cap) break;
             if (!have_w) {
                 w[0] = b[0];
                 w[1] = b[1];

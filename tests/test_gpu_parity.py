@@ -202,7 +202,7 @@ def test_anls_bpp_cycle_matches_oracle(h, name):
     V, W = p.V.copy(), p.W.copy()
     h.solve(p.M, gh, gw, V, W, "anls_bpp", levels=g["levels"], iters=g["K"], cycle=g["cycle"])
     f = o.objective(p.M, V, W)
-    assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
+    assert abs(f - g["objective"]) <= cycle_bar(g) * g["objective"], (f, g["objective"])
 
 
 def test_hals_ten_sweeps_track_oracle(h):
@@ -235,6 +235,20 @@ def test_error_matches_oracle(h, m, n, r):
 
 # ----------------------------- whole cycles -----------------------------------
 
+def cycle_bar(g):
+    """Objective bar of a stored cycle: 1e-3, except ANLS on a hierarchy whose coarsest grid has
+    fewer pixels than r: the W-step's NNLS problems there have many solutions (G = V^T V has rank
+    m_l < r; the GPU stops once its passive set spans the m_l rows, the oracle's FP64 active set
+    may take in further, dependent columns), each side's choice carries into the finer levels,
+    and the objective is compared at 1e-2, the coarse-level results against the optimality
+    conditions (test_anls_coarse_level_satisfies_kkt)."""
+    gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
+    cs = o.grid_hierarchy(gh, gw, g["levels"])[-1]
+    if g["algo"].startswith("anls") and cs[0] * cs[1] < r:
+        return 1e-2
+    return 1e-3
+
+
 @pytest.mark.parametrize("name", ["grid16_hals_L3_K100", "grid16_hals_L1_K100", "grid19_hals_L3_K500",
                                   "grid19_hals_L1_K500", "grid19_mu_L3_K500", "grid19_mu_L1_K500",
                                   "grid19_anls_L2_K8", "grid19_hals_fmg_L2_K100", "grid19_hals_ni_L2_K100",
@@ -246,15 +260,15 @@ def test_cycle_final_objective_matches_oracle(h, name):
     V, W = p.V.copy(), p.W.copy()
     h.solve(p.M, gh, gw, V, W, g["algo"], levels=g["levels"], iters=g["K"], cycle=g["cycle"])
     f = o.objective(p.M, V, W)
-    assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
+    assert abs(f - g["objective"]) <= cycle_bar(g) * g["objective"], (f, g["objective"])
     # the library's own error kernel agrees with the oracle's objective of the same iterate
     assert abs(h.error(p.M, V, W) - f) <= 1e-6 * f
 
 
 # The headline 19 x 19 workload at three levels with every algorithm and cycle.  Its coarsest
 # level has m_l = 25 < r = 49, where V is not unique; only the objective is compared
-# (1e-3 relative, as for every cycle), and the coarse-level ANLS results are checked for
-# the optimality conditions below instead.
+# (1e-3 relative, 1e-2 for ANLS: cycle_bar), and the coarse-level ANLS results are checked
+# for the optimality conditions below instead.
 HEADLINE_L3 = ["grid19_anls_L3_K8", "grid19_anls_L3_K500", "grid19_anls_L1_K500", "grid19_anls_fmg_L3_K8",
                "grid19_hals_fmg_L3_K100", "grid19_hals_ni_L3_K100", "grid19_mu_fmg_L3_K100",
                "grid19_hals_wcycle_L3_K100", "grid16_mu_wcycle_L3_K100"]
