@@ -487,10 +487,10 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
 # valid while the kernel's sources hash to `src`; the captures and their commands are
 # summarised under profiles/.
 TRAFFIC = {
-    "half_sweep_kernel": {"bytes": 0.5 * (4.968704e6 + 4.231680e6), "src": "bbc5f13c3f04b9cf",
+    "half_sweep_kernel": {"bytes": 0.5 * (4.969728e6 + 4.232192e6), "src": "a16cd947a6743266",
                           "files": ("fused.cu", "fused.cuh", "rowupdate.cuh", "ptx.cuh", "nmf_internal.cuh"),
                           "scope": "mean of the finest-level V-step (64-row tiles) and W-step (32-row tiles) launches, 19x19 grid n=2429 r=49"},
-    "tc_gemm_kernel": {"bytes": 267.997952e6 + 12.563712e6, "src": "3c5fffacd78e27f2",
+    "tc_gemm_kernel": {"bytes": 268.152832e6 + 12.926464e6, "src": "61770f2562ba1e3d",
                        "files": ("tc_gemm.cu", "tc_gemm.cuh", "ptx.cuh", "nmf_internal.cuh"),
                        "scope": "finest-level V-step product, 256x256 grid n=2000 r=64"},
 }

@@ -106,6 +106,18 @@ def test_sequence_workloads_match_oracle(h, name):
     assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
 
 
+def test_block_pivoting_column_vcycle_matches_active_set_oracle(h):
+    # ANLS by block principal pivoting on the sequence hierarchy (coarsest 4 x 4 grid, r = 10:
+    # every NNLS problem has a unique solution) against the active-set oracle run
+    g = GOLDEN["seq16_anls_cols_L3_K8"]
+    gh, gw, n, r, sigma = synth.SEQUENCE_WORKLOADS[g["workload"]]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma, sequence=True)
+    V, W = p.V.copy(), p.W.copy()
+    h.solve(p.M, gh, gw, V, W, "anls_bpp", levels=3, iters=8, coarsen_columns=True)
+    f = o.objective(p.M, V, W)
+    assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
+
+
 def test_column_vcycle_trace_and_stop_after(h):
     p = synth.make_problem(16, 16, 1024, 10, sigma=2.0, sequence=True)
     K = 20

@@ -134,6 +134,21 @@ def test_sample_against_fp64_oracle(h):
     print(f"grouped sample: max rel. error {worst:.2e}")
 
 
+def test_hals_and_mu_in_one_group(h):
+    # the update rule is a per-problem choice: a group mixing HALS and MU problems gives each
+    # the bits it gets in a group of its own algorithm
+    mixed = _group(WELL_POSED, "hals", 2, 6)
+    for i in (1, 3):
+        mixed[i][1]["algo"] = "mu"
+    res = h.solve_batch([d for _, d in mixed], grouped=True)
+    for i, (p, d) in enumerate(mixed):
+        alone = _group(WELL_POSED, d["algo"], 2, 6)[i][1]
+        r1 = h.solve_batch([alone], grouped=True)[0]
+        np.testing.assert_array_equal(alone["V"], d["V"])
+        np.testing.assert_array_equal(alone["W"], d["W"])
+        assert r1 == res[i]
+
+
 def test_stopping_rule(h):
     # each problem stops after the first watched sweep whose objective changed by at most
     # 1e-3 relative; the sweeps counted agree with the problem's own objective trace
