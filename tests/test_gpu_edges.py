@@ -63,3 +63,51 @@ def test_empty_inputs_rejected(h):
     # the handle stays usable
     p = synth.make_problem(4, 4, 8, 2, data_seed=1)
     h.solve(p.M, 4, 4, p.V.copy(), p.W.copy(), "hals", levels=2, iters=2)
+
+
+def _edge_check(h, p, V, W, Vo, Wo):
+    assert np.isfinite(V).all() and np.isfinite(W).all()
+    assert (V >= 0).all() and (W >= 0).all()
+    f, fo = o.objective(p.M, V, W), o.objective(p.M, Vo, Wo)
+    mnorm = float(np.linalg.norm(p.M.astype(np.float64)))
+    assert abs(f - fo) <= max(1e-4 * fo, 1e-6 * mnorm), (f, fo)
+
+
+@pytest.mark.parametrize("L,K", [(1, 3), (3, 4)])
+def test_edge_shapes_in_one_group(h, L, K):
+    # the HALS / MU edge shapes as one grouped solve (one pixel, one image, r = 1 and 64,
+    # grids too small to halve, a 1 x 37 strip)
+    cases = [c for c in CASES if c[6] != "anls"]
+    probs, batch = [], []
+    for gh, gw, n, r, _, _, algo in cases:
+        p = synth.make_problem(gh, gw, n, r, sigma=1.0, data_seed=11)
+        probs.append((p, algo))
+        batch.append(dict(M=p.M, grid_h=gh, grid_w=gw, V=p.V.copy(), W=p.W.copy(), algo=algo, levels=L, iters=K))
+    res = h.solve_batch(batch, grouped=True)
+    for (p, algo), d, (st, sweeps, obj) in zip(probs, batch, res):
+        assert st == 0
+        Vo, Wo = o.solve(p.M, p.grid_h, p.grid_w, p.V, p.W, algo, levels=L, K=K)
+        _edge_check(h, p, d["V"], d["W"], Vo, Wo)
+
+
+COLUMN_CASES = [  # (grid_h, grid_w, n, r, levels, K, algo): one image, two images, a strip, 4 levels
+    (1, 1, 1, 1, 3, 4, "hals"),
+    (3, 3, 2, 2, 3, 4, "hals"),
+    (1, 37, 70, 6, 3, 4, "mu"),
+    (5, 4, 7, 3, 4, 4, "anls"),
+]
+
+
+@pytest.mark.parametrize("case", COLUMN_CASES, ids=[f"{c[0]}x{c[1]}_n{c[2]}_r{c[3]}_L{c[4]}_{c[6]}" for c in COLUMN_CASES])
+def test_edge_column_vcycle_matches_oracle(h, case):
+    gh, gw, n, r, L, K, algo = case
+    p = synth.make_problem(gh, gw, n, r, sigma=1.0, data_seed=11, sequence=True)
+    V, W = p.V.copy(), p.W.copy()
+    h.solve(p.M, gh, gw, V, W, algo, levels=L, iters=K, coarsen_columns=True)
+    Vo, Wo = o.solve(p.M, gh, gw, p.V, p.W, algo, levels=L, K=K, coarsen_columns=True)
+    _edge_check(h, p, V, W, Vo, Wo)
+
+
+def test_empty_group_rejected(h):
+    with pytest.raises(native.NMFError, match="EINVAL"):
+        h.solve_batch([], grouped=True)
