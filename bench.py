@@ -60,7 +60,7 @@ def parse_args(argv=None):
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-rate-low", type=float, default=40.0)
     ap.add_argument("--serve-slots", type=int, default=8)
-    ap.add_argument("--serve-precisions", default="fp32,bf16,bf16_fp32_finish")
+    ap.add_argument("--serve-precisions", default="fp32,bf16,bf16_fp32_finish,auto")
     ap.add_argument("--serve-max-batches", default="16,1")
     ap.add_argument("--_oracle_sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -960,7 +960,8 @@ def oracle_sample_forms(sample, reps=3):
     stream = torch.cuda.current_stream()
     Mds = [torch.from_numpy(p.M).cuda() for _, p in sample]
     out = {"requests": len(sample), "source": "tests/golden/served_sample.json (FP64 oracle objectives)"}
-    for label, prec in (("fp32", native.NMF_FP32), ("bf16", native.NMF_BF16), ("bf16_fp32_finish", native.NMF_BF16_FP32)):
+    for label, prec in (("fp32", native.NMF_FP32), ("bf16", native.NMF_BF16), ("bf16_fp32_finish", native.NMF_BF16_FP32),
+                        ("auto", native.NMF_AUTO)):
         def reqs():
             return [dict(M=Md, grid_h=q["side"], grid_w=q["side"], V=p.V.copy(), W=p.W.copy(), algo=q["algo"],
                          levels=q["levels"], iters=q["iters"]) for (q, p), Md in zip(sample, Mds)]
@@ -1019,7 +1020,8 @@ def serving_form(args, pool):
                       "and V, W returned to it inside that time",
            "max_batch": "requests a slot takes at once (NMF_SERVE_MAX_BATCH): 16 = one graph per combination "
                         "of shapes, 1 = the cached graph of each shape"}
-    precs = {"fp32": native.NMF_FP32, "bf16": native.NMF_BF16, "bf16_fp32_finish": native.NMF_BF16_FP32}
+    precs = {"fp32": native.NMF_FP32, "bf16": native.NMF_BF16, "bf16_fp32_finish": native.NMF_BF16_FP32,
+             "auto": native.NMF_AUTO}
     for label in args.serve_precisions.split(","):
         prec = precs[label]
         for mb in (int(x) for x in args.serve_max_batches.split(",")):

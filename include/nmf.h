@@ -54,11 +54,20 @@ typedef enum {
 typedef enum {
     NMF_FP32 = 0,     /* everything float32 */
     NMF_BF16 = 1,     /* M, V, W as bfloat16 GEMM operands, float32 accumulation and updates */
-    NMF_BF16_FP32 = 2 /* NMF_BF16 for every sweep except the last quarter (at least one sweep) of the
+    NMF_BF16_FP32 = 2, /* NMF_BF16 for every sweep except the last quarter (at least one sweep) of the
                          last run of finest-level sweeps, which runs the float32 kernels on the
                          float32 M: the BF16 sweeps do most of the descent, the float32 ones remove
                          the bias that BF16 rounding of M leaves in the result.  With a stopping
                          rule (nmf_problem.rel_tol) only the float32 sweeps are watched. */
+    NMF_AUTO = 3      /* per problem: NMF_BF16_FP32 for HALS and MU problems whose grid has at least
+                         4096 pixels, NMF_FP32 otherwise (smaller grids, ANLS, and the entry points
+                         that take no algorithm).  Measured on the uneven request pool of the
+                         serving workload: below 64 x 64 pixels the float32 kernels (two launches
+                         per sweep) finish a request sooner than the BF16 form (six launches per
+                         sweep), and ANLS requests finish sooner in float32 at every size.  Under
+                         a light load this lowers the latency; a saturated server completes fewer
+                         requests per second than with NMF_BF16_FP32 (the float32 kernels take an
+                         SM each and share the GPU less well between concurrent requests). */
 } nmf_precision;
 
 /* Multigrid cycle (Section 4.3). */

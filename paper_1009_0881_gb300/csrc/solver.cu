@@ -179,6 +179,7 @@ struct Plan {
     unsigned* cbar = nullptr; // coarse runs: grid-barrier counter
     bool coarse_l0 = false;   // let level 0 use the coarse-run kernel too (nmf_profile_coarse)
     bool fixed_tiles = false; // keep the tile heights set by the caller (no tuning)
+    int algo_hint = -1;       // the problem's algorithm where the caller knows it (NMF_AUTO's choice)
     float* Gred = nullptr;    // grouped solves: reduced Gram matrix of the next half-sweep (r x rp)
     int* err_flag = nullptr;
     double* err_part = nullptr;
@@ -284,6 +285,7 @@ int pick_br(int rp) {
 }
 
 constexpr int kMaxSplits = 32;
+constexpr int64_t kAutoBf16Pixels = 4096;  // NMF_AUTO: smallest grid that takes the BF16 form
 
 // NMF_COARSE=0 runs coarse levels with the half-sweep kernels as well.
 bool coarse_enabled() {
@@ -793,6 +795,11 @@ void plan_dims(nmf_ctx* h, Plan& p, int64_t m, int64_t n, int gh, int gw, int r,
     p.rp = (int)round_up(r, 4);
     p.bf16 = h->prec != NMF_FP32;
     p.finish32 = h->prec == NMF_BF16_FP32;
+    if (h->prec == NMF_AUTO) {
+        // BF16 operands with float32 finishing where the products are large enough to pay for
+        // the form's extra launches (HALS / MU on grids of 64 x 64 pixels and more)
+        p.bf16 = p.finish32 = (p.algo_hint == NMF_HALS || p.algo_hint == NMF_MU) && m >= kAutoBf16Pixels;
+    }
     p.br = pick_br(p.rp);
     // W-step tile height chosen on the finest level (the W-step tiles and their Gram
     // slabs are shared by all levels); V-step tiles per level.  The BF16 form's row
@@ -1236,6 +1243,7 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     h->launches = 0;
 
     Plan p;
+    p.algo_hint = algo;
     rc = make_plan(h, p, m, n, gh, gw, r, L, trace ? opt->trace_len : 0);
     if (rc) return rc;
     rc = init_levels_padding(h, p);
@@ -1373,7 +1381,8 @@ cudaError_t enqueue_columns(nmf_ctx* h, std::vector<Plan>& plans, const ColumnLe
 int solve_columns_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw, int r, nmf_algo algo,
                        int L, int K, const nmf_options* opt, float* V, float* W) {
     if (opt->cycle != NMF_VCYCLE) return fail(h, NMF_EINVAL, "column coarsening runs the V-cycle only");
-    if (h->prec != NMF_FP32) return fail(h, NMF_EINVAL, "column coarsening runs in the FP32 form only");
+    if (h->prec != NMF_FP32 && h->prec != NMF_AUTO)
+        return fail(h, NMF_EINVAL, "column coarsening runs in the FP32 form only");
     const int64_t stop_after = opt->stop_after;
     const bool trace = opt->trace && opt->trace_len > 0;
     CK(cudaSetDevice(h->device));
@@ -1493,8 +1502,10 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
     CK(cudaSetDevice(h->device));
     h->launches = 0;
     std::vector<Plan> plans(count);
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
+        plans[i].algo_hint = probs[i].algo;
         plan_dims(h, plans[i], probs[i].m, probs[i].n, probs[i].grid_h, probs[i].grid_w, probs[i].r, probs[i].levels, 0);
+    }
     int rc = make_plans(h, plans);
     if (rc) return rc;
     for (int i = 0; i < count; ++i) {
@@ -1635,7 +1646,8 @@ int grouped_impl(nmf_ctx* h, nmf_problem* probs, int count) {
     if (!h) return NMF_EINVAL;
     int rc = check_problems(h, probs, count);
     if (rc) return rc;
-    if (h->prec != NMF_FP32) return fail(h, NMF_EINVAL, "the grouped form runs in the FP32 form only");
+    if (h->prec != NMF_FP32 && h->prec != NMF_AUTO)
+        return fail(h, NMF_EINVAL, "the grouped form runs in the FP32 form only");
     const nmf_problem& q0 = probs[0];
     for (int i = 0; i < count; ++i) {
         const nmf_problem& q = probs[i];
@@ -1834,7 +1846,7 @@ extern "C" {
 int nmf_create(nmf_handle* out, int device, size_t hbm_budget_bytes, nmf_precision prec) {
     if (!out) return NMF_EINVAL;
     *out = nullptr;
-    if (prec != NMF_FP32 && prec != NMF_BF16 && prec != NMF_BF16_FP32) return NMF_EINVAL;
+    if (prec != NMF_FP32 && prec != NMF_BF16 && prec != NMF_BF16_FP32 && prec != NMF_AUTO) return NMF_EINVAL;
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
         cudaGetLastError();
@@ -1926,6 +1938,7 @@ int64_t nmf_workspace_bytes(nmf_handle h, const nmf_problem* probs, int count) {
         if (q->grid_h < 1 || q->grid_w < 1 || (int64_t)q->grid_h * q->grid_w != q->m || q->levels < 1 ||
             q->levels > 16)
             return fail(h, NMF_EINVAL, "problem %d: bad geometry", i);
+        plans[i].algo_hint = q->algo;
         plan_dims(h, plans[i], q->m, q->n, q->grid_h, q->grid_w, q->r, q->levels, 0);
     }
     return (int64_t)plans_bytes(h, plans);
@@ -2095,6 +2108,7 @@ int nmf_profile_sweep(nmf_handle h, const float* M, int64_t m, int64_t n, int r,
     CK(cudaSetDevice(h->device));
     h->launches = 0;
     Plan p;
+    p.algo_hint = algo;
     rc = make_plan(h, p, m, n, (int)m, 1, r, 1, 0);
     if (rc) return rc;
     rc = stage_problem(h, p, M, V, W, !p.bf16 || p.finish32);

@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 NMF_HALS, NMF_MU, NMF_ANLS, NMF_ANLS_BPP = 0, 1, 2, 3
-NMF_FP32, NMF_BF16, NMF_BF16_FP32 = 0, 1, 2
+NMF_FP32, NMF_BF16, NMF_BF16_FP32, NMF_AUTO = 0, 1, 2, 3
 NMF_VCYCLE, NMF_NESTED, NMF_FMG, NMF_WCYCLE = 0, 1, 2, 3
 NMF_OK, NMF_EINVAL, NMF_ENOMEM, NMF_ENOCONV, NMF_ECUDA, NMF_ETIMEOUT, NMF_EBUSY, NMF_ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 ALGOS = {"hals": NMF_HALS, "mu": NMF_MU, "anls": NMF_ANLS, "anls_bpp": NMF_ANLS_BPP}
