@@ -893,6 +893,7 @@ def batched_form(args, pool, reps=3):
     out = {"problems": len(pool), "levels": BATCH_LEVELS, "iters_cap": BATCH_ITERS["hals"], "rel_tol": BATCH_TOL,
            "algo": "hals", "flops_per_batch_note": "sum over problems of the Appendix A.1 sweep cost"}
     for label, prec, batched in (("batched_fp32", native.NMF_FP32, True), ("batched_bf16", native.NMF_BF16, True),
+                                 ("batched_bf16_fp32_finish", native.NMF_BF16_FP32, True),
                                  ("grouped_fp32", native.NMF_FP32, "grouped"),
                                  ("sequential_plain_fp32", native.NMF_FP32, False)):
         with native.Handle(0, precision=prec) as hh:
@@ -926,6 +927,8 @@ def batched_form(args, pool, reps=3):
                                                       / out["batched_fp32"]["ms_per_batch"])
     out["speedup_grouped_fp32_vs_sequential_fp32"] = (out["sequential_plain_fp32"]["ms_per_batch"]
                                                       / out["grouped_fp32"]["ms_per_batch"])
+    out["speedup_batched_bf16_fp32_finish_vs_sequential_fp32"] = (out["sequential_plain_fp32"]["ms_per_batch"]
+                                                                  / out["batched_bf16_fp32_finish"]["ms_per_batch"])
     del Mds, V0s, W0s, Vs, Ws
     torch.cuda.empty_cache()
     return out
