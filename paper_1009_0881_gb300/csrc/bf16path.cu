@@ -66,6 +66,8 @@ __global__ void to_bf16_t_kernel(const float* __restrict__ in, int64_t ldi, int6
 // (ticket in cnt[x], reset afterwards) adds the chunk sums in chunk order.
 __global__ void gram_final_kernel(const float* __restrict__ slabs, int count, int64_t stride, int n,
                                   float* __restrict__ G, float* __restrict__ part, int* cnt, const int* skip) {
+    ptx::grid_dependency_wait();  // the slabs and the flag come from the previous kernel
+    ptx::launch_dependents();
     if (skip && *(volatile const int*)skip) return;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int S = gridDim.y, y = blockIdx.y;
@@ -218,6 +220,8 @@ template <int MODE, int BA>
 __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) {
     constexpr int TLD = tld<BA>();
     extern __shared__ __align__(16) float sm[];
+    ptx::grid_dependency_wait();  // the products, the Gram matrix and the flag come from earlier kernels
+    ptx::launch_dependents();
     if (q.skip && *(volatile const int*)q.skip) return;  // converged problem: nothing to do
     const int r = q.r, rp = q.rp;
     float* Gs = sm;                       // r x rp
@@ -328,6 +332,23 @@ __global__ void __launch_bounds__(NT, 1) rows_update_kernel(const RowsParams q) 
     }
 }
 
+// Launch with programmatic stream serialization: the kernel may start while the previous one
+// finishes; it waits (griddepcontrol.wait) before reading that kernel's results.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 size_t rows_smem_bytes(int r, int rp, int ba) {
     return sizeof(float) * ((size_t)r * rp + kMaxRank + 3 * ba * kMaxRank + kMaxRank * (ba + 1) + kMaxRank * GRS);
 }
@@ -357,9 +378,8 @@ cudaError_t gram_final_launch(const float* slabs, int count, int64_t stride, int
                               int* cnt, cudaStream_t st, const int* skip) {
     const int n = r * rp;
     const int S = (int)std::min<int64_t>(kGramChunks, std::max<int64_t>(1, ceil_div(count, 16)));
-    gram_final_kernel<<<dim3((unsigned)ceil_div(n, 256), (unsigned)S), 256, 0, st>>>(slabs, count, stride, n, G, part,
-                                                                                     cnt, skip);
-    return cudaGetLastError();
+    return launch_pdl(gram_final_kernel, dim3((unsigned)ceil_div(n, 256), (unsigned)S), dim3(256), 0, st, slabs, count,
+                      stride, n, G, part, cnt, skip);
 }
 
 template <int BA>
@@ -383,27 +403,22 @@ cudaError_t rows_update_init() {
 }
 
 template <int BA>
-void rows_update_launch_ba(const RowsParams& q, int mode, cudaStream_t st) {
+cudaError_t rows_update_launch_ba(const RowsParams& q, int mode, cudaStream_t st) {
     const size_t smem = rows_smem_bytes(q.r, q.rp, BA);
     const unsigned grid = (unsigned)ceil_div(q.rows, BA);
     switch (mode) {
-        case rowupd::kModeHals: rows_update_kernel<rowupd::kModeHals, BA><<<grid, NT, smem, st>>>(q); break;
-        case rowupd::kModeMu: rows_update_kernel<rowupd::kModeMu, BA><<<grid, NT, smem, st>>>(q); break;
-        default: rows_update_kernel<rowupd::kModeStore, BA><<<grid, NT, smem, st>>>(q); break;
+        case rowupd::kModeHals: return launch_pdl(rows_update_kernel<rowupd::kModeHals, BA>, dim3(grid), dim3(NT), smem, st, q);
+        case rowupd::kModeMu: return launch_pdl(rows_update_kernel<rowupd::kModeMu, BA>, dim3(grid), dim3(NT), smem, st, q);
+        default: return launch_pdl(rows_update_kernel<rowupd::kModeStore, BA>, dim3(grid), dim3(NT), smem, st, q);
     }
 }
 
 cudaError_t rows_update_launch(const RowsParams& q, int mode, cudaStream_t st) {
     if (q.rows <= 0) return cudaSuccess;
-    if (q.ba == 16)
-        rows_update_launch_ba<16>(q, mode, st);
-    else if (q.ba == 32)
-        rows_update_launch_ba<32>(q, mode, st);
-    else if (q.ba == 64)
-        rows_update_launch_ba<64>(q, mode, st);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    if (q.ba == 16) return rows_update_launch_ba<16>(q, mode, st);
+    if (q.ba == 32) return rows_update_launch_ba<32>(q, mode, st);
+    if (q.ba == 64) return rows_update_launch_ba<64>(q, mode, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace nmfk

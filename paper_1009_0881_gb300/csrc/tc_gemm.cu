@@ -95,6 +95,10 @@ __global__ void __launch_bounds__(128, 2)
     uint64_t* done = empty + NSTAGE;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
 
+    // programmatic dependent launch: the launch overlaps the end of the previous kernel,
+    // everything below (the factor operand, the skip flag) waits for its results
+    ptx::grid_dependency_wait();
+    ptx::launch_dependents();
     if (p.skip && *(volatile const int*)p.skip) return;  // converged problem: nothing to do
     const int warp = threadIdx.x >> 5;
     const int m0 = blockIdx.x * TM_ROWS;
@@ -195,9 +199,17 @@ cudaError_t set_attr_t() {
 
 template <int BN>
 cudaError_t launch_t(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmParams& p, cudaStream_t st) {
-    dim3 grid((unsigned)((p.Ma + TM_ROWS - 1) / TM_ROWS), (unsigned)p.splits);
-    tc_gemm_kernel<BN><<<grid, 128, smem_bytes_t<BN>(), st>>>(tmA, tmB, p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((p.Ma + TM_ROWS - 1) / TM_ROWS), (unsigned)p.splits);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem_bytes_t<BN>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN>, tmA, tmB, p);
 }
 
 }  // namespace
