@@ -7,6 +7,7 @@
 // Cholesky factor of the passive block grown column by column (HALS and MU are
 // updated inside the fused half-sweep kernel and the BF16 row kernel).
 #include "nmf_internal.cuh"
+#include "ptx.cuh"
 
 namespace nmfk {
 
@@ -234,6 +235,8 @@ __host__ __device__ inline size_t anls_warp_doubles(int r) { return (size_t)r * 
 // G = sum of the Gram partial slabs in FP64 (slabs in index order), once per
 // half-sweep, for all the ANLS rows.
 __global__ void gram_reduce_f64_kernel(const UpdateArgs u) {
+    ptx::grid_dependency_wait();  // the slabs and the flag come from the previous kernel
+    ptx::launch_dependents();
     if (u.skip && *(volatile const int*)u.skip) return;
     const int r = u.r;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -248,6 +251,8 @@ __global__ void gram_reduce_f64_kernel(const UpdateArgs u) {
 template <bool BPP>
 __global__ void __launch_bounds__(32 * kAnlsWarps) anls_rows_kernel(const UpdateArgs u, int* status) {
     extern __shared__ double smem[];
+    ptx::grid_dependency_wait();  // G, the products and the flag come from earlier kernels
+    ptx::launch_dependents();
     if (u.skip && *(volatile const int*)u.skip) return;  // same value in every CTA
     const int r = u.r;
     double* G = smem;  // r x r
@@ -452,10 +457,31 @@ cudaError_t init_kernel_attributes() {
     return e;
 }
 
+namespace {
+// Launch with programmatic stream serialization: the kernel may start while the previous one
+// finishes; it waits (griddepcontrol.wait) before reading that kernel's results.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+}  // namespace
+
 cudaError_t anls_update_launch(const UpdateArgs& u, int num_sms, int* d_status, cudaStream_t st) {
     if (u.rows <= 0) return cudaSuccess;
     if (!u.Gd) return cudaErrorInvalidValue;
-    gram_reduce_f64_kernel<<<(unsigned)ceil_div((int64_t)u.r * u.r, 256), 256, 0, st>>>(u);
+    cudaError_t e = launch_pdl(gram_reduce_f64_kernel, dim3((unsigned)ceil_div((int64_t)u.r * u.r, 256)), dim3(256), 0,
+                               st, u);
+    if (e != cudaSuccess) return e;
     // one warp per row, FP64-bound: fewer warps per CTA when the rows would not reach every
     // SM with kAnlsWarps per CTA (the rows of a coarse level's V-step, for example)
     int nw = kAnlsWarps;
@@ -464,11 +490,8 @@ cudaError_t anls_update_launch(const UpdateArgs& u, int num_sms, int* d_status, 
     int64_t grid = ceil_div(u.rows, nw);
     const int64_t cap = 8LL * num_sms * (kAnlsWarps / nw);
     if (grid > cap) grid = cap;
-    if (u.bpp)
-        anls_rows_kernel<true><<<(unsigned)grid, 32 * nw, smem, st>>>(u, d_status);
-    else
-        anls_rows_kernel<false><<<(unsigned)grid, 32 * nw, smem, st>>>(u, d_status);
-    return cudaGetLastError();
+    if (u.bpp) return launch_pdl(anls_rows_kernel<true>, dim3((unsigned)grid), dim3(32 * nw), smem, st, u, d_status);
+    return launch_pdl(anls_rows_kernel<false>, dim3((unsigned)grid), dim3(32 * nw), smem, st, u, d_status);
 }
 
 }  // namespace nmfk
