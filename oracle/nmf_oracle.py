@@ -471,6 +471,40 @@ def vcycle(Ms, grids, V, W, algo: str, L: int, K: int, level: int = 0, hooks=Non
     return smooth(M, V, W, algo, K // 2, trace, level + 1)
 
 
+# Algorithm V-cycle states its budgets as time: T/4 of smoothing before the restriction, T/4
+# for the coarser V-cycle, T/2 of smoothing after the prolongation, all of T on the coarsest
+# level.  READING: with per-sweep costs c_l of levels l = 1 (finest) .. L, level l < L receives
+# T_l = T / 4^(l-1) and runs floor(T_l / (4 c_l)) sweeps before and floor(T_l / (2 c_l)) after,
+# the coarsest floor(T_L / c_L).  Table 1's sweep counts are this split for c_l = c_1 / 4^(l-1)
+# with T = K c_1; other costs (the measured ones of a machine) give other counts.
+
+def time_schedule(T: float, costs) -> tuple[list[int], int, list[int]]:
+    """(pre, coarse, post): sweeps of levels 1..L-1 before and after the coarser cycle, and of
+    level L, for a V-cycle of total time T with per-sweep costs costs[l-1] (any common unit)."""
+    L = len(costs)
+    pre, post = [], []
+    for l in range(L - 1):
+        Tl = T / 4.0 ** l
+        pre.append(int(np.floor(Tl / (4.0 * costs[l]) + 1e-9)))
+        post.append(int(np.floor(Tl / (2.0 * costs[l]) + 1e-9)))
+    coarse = int(np.floor(T / 4.0 ** (L - 1) / costs[L - 1] + 1e-9))
+    return pre, coarse, post
+
+
+def vcycle_counts(Ms, grids, V, W, algo: str, pre, coarse: int, post, level: int = 0, trace=None):
+    """Algorithm V-cycle with explicit sweep counts per level (time_schedule): pre[level]
+    sweeps, restriction of V, the coarser cycle, prolongation of V, post[level] sweeps; the
+    coarsest level (level == len(pre)) runs `coarse` sweeps."""
+    M = Ms[level]
+    if level == len(pre):
+        return smooth(M, V, W, algo, coarse, trace, level + 1)
+    V, W = smooth(M, V, W, algo, pre[level], trace, level + 1)
+    Vc = restrict(V, *grids[level])
+    Vc, W = vcycle_counts(Ms, grids, Vc, W, algo, pre, coarse, post, level + 1, trace)
+    V = prolong(Vc, *grids[level + 1], *grids[level])
+    return smooth(M, V, W, algo, post[level], trace, level + 1)
+
+
 def nested_iteration(Ms, grids, V0, W0, algo: str, L: int, K: int, level: int = 0, trace=None, hooks=None):
     """Algorithm NI: solve on the coarser level (K coarse sweeps), prolong, then floor(3K/4) sweeps.
 
@@ -584,11 +618,13 @@ def vcycle_both(Ms, grids, ns, V, W, algo: str, L: int, K: int, level: int = 0, 
 
 
 def solve(M, grid_h: int, grid_w: int, V0, W0, algo: str = "hals", levels: int = 1, K: int = 100,
-          cycle: str = "vcycle", trace=None, precision: str = "fp64", coarsen_columns: bool = False):
+          cycle: str = "vcycle", trace=None, precision: str = "fp64", coarsen_columns: bool = False,
+          level_sweeps=None):
     """Multilevel NMF of M (m = grid_h * grid_w rows) from (V0, W0); returns (V, W).
 
     precision: "fp64" (default), "fp32" or "bf16" (see PRECISION).  coarsen_columns: the
-    V-cycle coarsens the columns of M as a sequence too (vcycle_both)."""
+    V-cycle coarsens the columns of M as a sequence too (vcycle_both).  level_sweeps: a
+    V-cycle with explicit counts (pre, coarse, post) as time_schedule returns them (K unused)."""
     global PRECISION
     M = np.asarray(M, dtype=np.float64)
     Ms = restrict_hierarchy(M, grid_h, grid_w, levels)
@@ -598,6 +634,10 @@ def solve(M, grid_h: int, grid_w: int, V0, W0, algo: str = "hals", levels: int =
     saved = PRECISION
     PRECISION = {"fp64": None, "fp32": "fp32", "bf16": "bf16"}[precision]
     try:
+        if level_sweeps is not None:
+            pre, coarse, post = level_sweeps
+            assert cycle == "vcycle" and len(pre) == len(post) == levels - 1
+            return vcycle_counts(Ms, grids, V, W, algo, list(pre), int(coarse), list(post), trace=trace)
         if coarsen_columns:
             assert cycle == "vcycle", "column coarsening is defined for the V-cycle"
             Ms = restrict_hierarchy_both(M, grid_h, grid_w, levels)

@@ -57,11 +57,21 @@ CASES = [
     ("seq32_hals_cols_L4_K100", "seq32_n4096_r16", "hals", 4, 100, "vcycle_cols"),
     ("seq32_hals_L3_K100", "seq32_n4096_r16", "hals", 3, 100, "vcycle"),
     ("seq32_hals_L1_K100", "seq32_n4096_r16", "hals", 1, 100, "vcycle"),
+    # V-cycles with explicit per-level counts (the time split of Algorithm V-cycle with
+    # measured per-sweep costs): see LEVEL_SWEEPS
+    ("grid19_hals_timed_L3", "grid19_n2429_r49", "hals", 3, 0, "vcycle_counts"),
+    ("grid19_mu_timed_L3", "grid19_n2429_r49", "mu", 3, 0, "vcycle_counts"),
     # ANLS on the sequence: the W-step's n rows shrink with the columns (Section 6.1)
     ("seq32_anls_L1_K20", "seq32_n4096_r16", "anls", 1, 20, "vcycle"),
     ("seq32_anls_L3_K20", "seq32_n4096_r16", "anls", 3, 20, "vcycle"),
     ("seq32_anls_cols_L3_K20", "seq32_n4096_r16", "anls", 3, 20, "vcycle_cols"),
 ]
+
+
+# (pre, coarse, post) of the explicit-count cases: the split of T = 500 finest-sweep times with
+# per-sweep costs 28.0 / 22.4 / 16.3 us (19x19 / 10x10 / 5x5 levels, as measured on the GPU)
+LEVEL_SWEEPS = {"grid19_hals_timed_L3": ([125, 39], 53, [250, 78]),
+                "grid19_mu_timed_L3": ([125, 39], 53, [250, 78])}
 
 
 def _problem(wl):
@@ -73,7 +83,9 @@ def _problem(wl):
     return h, w, synth.make_problem(h, w, n, r, sigma=sigma)
 
 
-def _solve(p, h, w, algo, L, K, cyc, **kw):
+def _solve(p, h, w, algo, L, K, cyc, name=None, **kw):
+    if cyc == "vcycle_counts":
+        return o.solve(p.M, h, w, p.V, p.W, algo, levels=L, level_sweeps=LEVEL_SWEEPS[name], **kw)
     if cyc == "vcycle_cols":
         return o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, coarsen_columns=True, **kw)
     return o.solve(p.M, h, w, p.V, p.W, algo, levels=L, K=K, cycle=cyc, **kw)
@@ -103,7 +115,7 @@ def _fp32_child(name):
         if nm == name:
             h, w, p = _problem(wl)
             try:
-                V, W = _solve(p, h, w, algo, L, K, cyc, precision="fp32")
+                V, W = _solve(p, h, w, algo, L, K, cyc, name=nm, precision="fp32")
                 print(repr(o.objective(p.M.astype(np.float64), V, W)))
             except o.NNLSNotConverged:
                 print("None")
@@ -129,10 +141,12 @@ def main(only=None):
             continue
         h, w, p = _problem(wl)
         t = time.time()
-        V, W = _solve(p, h, w, algo, L, K, cyc)
+        V, W = _solve(p, h, w, algo, L, K, cyc, name=name)
         f = o.objective(p.M.astype(np.float64), V, W)
         entry = {"workload": wl, "algo": algo, "levels": L, "K": K, "cycle": cyc, "objective": f,
                  "norm_M": float(np.linalg.norm(p.M.astype(np.float64)))}
+        if cyc == "vcycle_counts":
+            entry["level_sweeps"] = LEVEL_SWEEPS[name]
         if name in FP32_PRODUCT_CASES:
             # the oracle at float32 precision with two summation orders of its float32 matrix
             # products (the library matmul on one thread and on four): on these cycles the two

@@ -220,3 +220,47 @@ def test_wcycle_data_flow():
     Vf, Wf = o.smooth(Ms[0], o.prolong(Vc, *grids[1], *grids[0]), Wc, "hals", K // 2)
     np.testing.assert_array_equal(V, Vf)
     np.testing.assert_array_equal(W, Wf)
+
+
+# ---------------------------------------------------------------- time budgets
+# Algorithm V-cycle gives its levels shares of a time T (T/4 before, T/4 to the coarser
+# cycle, T/2 after); Table 1 is that split when a sweep on a level costs a quarter of one
+# on the level above.
+
+@pytest.mark.parametrize("L,K", [(2, 8), (3, 100), (3, 500), (4, 40), (5, 12)])
+def test_time_split_with_quarter_costs_is_table1(L, K):
+    costs = [0.25 ** l for l in range(L)]
+    pre, coarse, post = o.time_schedule(K * costs[0], costs)
+    assert pre == [K // 4] * (L - 1) and post == [K // 2] * (L - 1) and coarse == K
+
+
+def test_time_split_by_hand():
+    # T = 1000, costs 10 / 8 / 5: level 1 gets 1000 (250 before, 500 after: 25 and 50
+    # sweeps), level 2 gets 250 (62.5 / 8 -> 7 before, 125 / 8 -> 15 after), level 3 gets
+    # 62.5 (62.5 / 5 -> 12 sweeps)
+    assert o.time_schedule(1000.0, [10.0, 8.0, 5.0]) == ([25, 7], 12, [50, 15])
+    # one level: all of T
+    assert o.time_schedule(90.0, [7.0]) == ([], 12, [])
+
+
+def test_explicit_counts_with_table1_counts_are_the_vcycle():
+    p = synth.make_problem(9, 9, 30, 4, data_seed=13)
+    for algo in ("hals", "mu"):
+        a = o.solve(p.M, 9, 9, p.V, p.W, algo, levels=3, K=8)
+        b = o.solve(p.M, 9, 9, p.V, p.W, algo, levels=3, level_sweeps=([2, 2], 8, [4, 4]))
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_explicit_counts_order():
+    # level of every sweep in the order the cycle runs them, with distinct counts
+    p = synth.make_problem(16, 16, 4, 2, data_seed=1)
+    trace = []
+    orig = dict(o.SWEEPS)
+    o.SWEEPS["count"] = lambda M, V, W: (V, W)
+    try:
+        o.solve(p.M, 16, 16, p.V, p.W, algo="count", levels=3, level_sweeps=([1, 2], 3, [5, 4]), trace=trace)
+    finally:
+        o.SWEEPS.clear()
+        o.SWEEPS.update(orig)
+    assert [lvl for lvl, _ in trace] == [1] + [2] * 2 + [3] * 3 + [2] * 4 + [1] * 5

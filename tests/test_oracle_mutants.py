@@ -222,6 +222,17 @@ def _vcycle_both_w_injected(Ms, grids, ns, V, W, algo, L, K, level=0, trace=None
         o.prolong_columns = saved
 
 
+def _time_schedule_half_to_coarse(T, costs):
+    # the coarser cycle given T/2 instead of T/4 of each level's time
+    L = len(costs)
+    pre, post = [], []
+    for l in range(L - 1):
+        Tl = T / 2.0 ** l
+        pre.append(int(np.floor(Tl / (4.0 * costs[l]) + 1e-9)))
+        post.append(int(np.floor(Tl / (2.0 * costs[l]) + 1e-9)))
+    return pre, int(np.floor(T / 2.0 ** (L - 1) / costs[L - 1] + 1e-9)), post
+
+
 def _table1_checks():
     return [lambda row=row: tc.test_vcycle_sweep_allocation_matches_table1(row) for row in tc._table1_rows()]
 
@@ -261,6 +272,9 @@ MUTANTS = {
                                                   lambda: tcol.test_pixel_operators_are_tensor_products_of_the_column_operators(4, 5)]),
     "column V-cycle prolongs W by injection": ("vcycle_both", _vcycle_both_w_injected,
                                                [lambda: tcol.test_column_vcycle_data_flow("hals")]),
+    "time split gives the coarser cycle half": ("time_schedule", _time_schedule_half_to_coarse,
+                                                [tc.test_time_split_by_hand,
+                                                 lambda: tc.test_time_split_with_quarter_costs_is_table1(3, 100)]),
     "W-cycle visits the coarser level once": ("wcycle", _wcycle_single_visit,
                                               [tc.test_wcycle_order_visits_the_coarser_level_twice,
                                                tc.test_wcycle_data_flow]),
