@@ -470,6 +470,8 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
             out["time_to_target_table"] = time_to_target_table(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw)
         if not args.no_sequence_table:
             out["image_sequence"] = sequence_table(h, stream, golden)
+        out["time_split_vcycle"] = {a: time_split_vcycle(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw, a)
+                                    for a in ("hals", "mu")}
     if not args.no_precision_form:
         out["precision_form"] = precision_form(args)
     if not args.no_batched_form:
@@ -508,7 +510,8 @@ def _traffic(kernel):
     return t["bytes"] if hsh.hexdigest()[:16] == t["src"] else None
 
 
-def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, reps=3, warm=1, cols=False):
+def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, reps=3, warm=1, cols=False,
+                   level_sweeps=None):
     """Wall time of a V-cycle solve (device-resident inputs, CUDA events) until the finest-level
     objective first reaches (1 + 1e-3) f*, f* the FP64 oracle's final objective for the same
     (algo, L, K): the per-sweep trace locates that sweep, then solves stopped right after it
@@ -519,11 +522,18 @@ def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, r
 
     from paper_1009_0881_gb300 import native
 
-    sched = native.schedule("vcycle", L, K)
+    if level_sweeps is None:
+        sched = native.schedule("vcycle", L, K)
+        pre = K // 4 if L > 1 else K
+    else:
+        pre_c, coarse_c, post_c = level_sweeps
+        sched = [pre_c[0] + post_c[0]] + [pre_c[l] + post_c[l] for l in range(1, L - 1)] + [coarse_c]
+        pre = pre_c[0]
     target = (1 + 1e-3) * fstar
     Vd.copy_(V0d)
     Wd.copy_(W0d)
-    tr = h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, trace_len=sched[0], coarsen_columns=cols)
+    kw = {"level_sweeps": level_sweeps} if level_sweeps is not None else {}
+    tr = h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, trace_len=sched[0], coarsen_columns=cols, **kw)
     hit = np.nonzero(tr <= target)[0]
     res = {"algo": algo, "levels": L, "iters": K, "oracle_fp64": fstar, "objective_target": target,
            "final_objective_gpu": float(tr[-1]) if len(tr) else None}
@@ -531,7 +541,6 @@ def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, r
         res["ms"] = None
         return res
     s_fine = int(hit[0]) + 1
-    pre = K // 4 if L > 1 else K
     stop = s_fine if s_fine <= pre else s_fine + sum(sched[1:])
     ms = []
     for it in range(warm + reps):
@@ -540,7 +549,7 @@ def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, r
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, stop_after=stop, coarsen_columns=cols)
+        h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, stop_after=stop, coarsen_columns=cols, **kw)
         e1.record(stream)
         e1.synchronize()
         if it >= warm:
@@ -549,6 +558,68 @@ def time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, fstar, r
     res.update(ms=statistics.median(ms), sweeps=stop, fine_sweeps=s_fine, objective_at_stop=f,
                reached=bool(f <= target * (1 + 1e-12)))
     return res
+
+
+def _solve_ms(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, reps=3, **kw):
+    """Median CUDA-event time of a solve from the initial iterate (one untimed run first)."""
+    import torch
+
+    ms = []
+    for it in range(reps + 1):
+        Vd.copy_(V0d)
+        Wd.copy_(W0d)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.solve(Md, gh, gw, Vd, Wd, algo, levels=L, iters=K, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        if it:
+            ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def time_split_vcycle(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw, algo="hals"):
+    """Algorithm V-cycle with its time budgets taken as time (T/4 before, T/4 to the coarser
+    cycle, T/2 after): the per-sweep cost of each level is measured here, inside solves with
+    explicit counts (100 extra sweeps on one level against a one-sweep-per-run cycle, median of
+    three), the budget is the time of the single-level run's K sweeps, and nmf_time_schedule
+    turns both into counts.  Reported: the counts, the time and objective of that V-cycle, the
+    single-level run's, and the V-cycle's time to the single-level run's target."""
+    from paper_1009_0881_gb300 import native
+
+    L, K, extra = args.levels, args.iters, 100
+    base = ([1] * (L - 1), 1, [1] * (L - 1))
+    t0 = _solve_ms(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, level_sweeps=base)
+    costs = []
+    for lvl in range(L):
+        pre, coarse, post = [list(x) if isinstance(x, list) else x for x in base]
+        if lvl == L - 1:
+            coarse += extra
+        else:
+            post[lvl] += extra
+        t = _solve_ms(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, level_sweeps=(pre, coarse, post))
+        costs.append(max(t - t0, 1e-6) / extra)
+    budget = K * costs[0]
+    counts = native.time_schedule(budget, costs)
+    ms_ml = _solve_ms(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, level_sweeps=counts)
+    f_ml = h.error(Md, Vd, Wd)
+    ms_sl = _solve_ms(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, 1, K)
+    f_sl = h.error(Md, Vd, Wd)
+    out = {"algo": algo, "levels": L, "budget_fine_sweeps": K, "sweep_cost_ms_per_level": costs,
+           "level_sweeps": {"pre": counts[0], "coarse": counts[1], "post": counts[2]},
+           "multilevel": {"ms": ms_ml, "objective": f_ml}, "single_level": {"ms": ms_sl, "objective": f_sl}}
+    g = golden.get(f"grid19_{algo}_timed_L3", {})
+    if args.workload == WORKLOAD and g.get("level_sweeps") and [list(x) if isinstance(x, list) else x
+                                                                for x in g["level_sweeps"]] == list(counts):
+        out["multilevel"]["oracle_fp64"] = g["objective"]
+        out["multilevel"]["rel_diff"] = abs(f_ml - g["objective"]) / g["objective"]
+    f1 = golden.get(f"grid19_{algo}_L1_K{K}", {}).get("objective") if args.workload == WORKLOAD else None
+    if f1 is not None:
+        t = time_to_target(h, Md, V0d, W0d, Vd, Wd, stream, gh, gw, algo, L, K, f1, level_sweeps=counts)
+        out["multilevel_to_single_level_target"] = {k: t.get(k) for k in ("objective_target", "ms", "sweeps",
+                                                                         "fine_sweeps", "reached")}
+    return out
 
 
 def time_to_target_table(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw):

@@ -118,6 +118,12 @@ typedef struct {
                              fine sweep. */
     int64_t trace_len;    /* capacity of trace; entries beyond it are not written */
     int64_t* trace_count; /* optional: receives the number of fine-level sweeps run */
+    const int64_t* level_sweeps; /* optional: a V-cycle with these sweep counts per level instead of
+                             the counts iters gives (Table 1): 2 levels - 1 entries in the order
+                             the cycle runs them, before-sweeps of levels 1 .. L-1, the coarsest
+                             level, after-sweeps of levels L-1 .. 1 (nmf_time_schedule computes
+                             them from a time budget); each >= 0.  V-cycle only, not with
+                             coarsen_columns (NMF_EINVAL). */
     int coarsen_columns;  /* nonzero: the columns of M form a sequence that varies smoothly
                              (Section 6.1: video frames, spectral bands) and are coarsened too:
                              level l has ceil(n_{l-1}/2) columns, M_{l+1} = R M_l R_n^T, and W
@@ -244,6 +250,21 @@ int nmf_error(nmf_handle h, const float* M, const float* V, const float* W,
  *   total, or a negative nmf_status.
  */
 int64_t nmf_schedule(nmf_cycle cycle, int levels, int iters, int64_t* sweeps_per_level);
+
+/*
+ * nmf_time_schedule - host-side split of a V-cycle's time budget over its levels (no device
+ * work).  Algorithm V-cycle (Section 4.3) gives a level with time T_l a quarter of it for
+ * sweeps before the restriction, a quarter for the coarser cycle and half for sweeps after
+ * the prolongation; the coarsest level spends all of its T_L.  With T_1 = budget and the
+ * cost of one sweep on level l in costs[l-1] (same unit as budget, > 0), level l < L runs
+ * floor(T_l / (4 costs[l-1])) sweeps before and floor(T_l / (2 costs[l-1])) after, the
+ * coarsest floor(T_L / costs[L-1]).  Table 1 is this split when every level's sweep costs a
+ * quarter of the one above (then the counts are floor(K/4), K, floor(K/2) for
+ * budget = K costs[0]).  Writes the 2 levels - 1 counts in the order the cycle runs them
+ * (before-sweeps of levels 1 .. L-1, the coarsest level, after-sweeps of levels L-1 .. 1)
+ * to level_sweeps_out, for nmf_options.level_sweeps.  Returns NMF_OK or NMF_EINVAL.
+ */
+int nmf_time_schedule(int levels, double budget, const double* costs, int64_t* level_sweeps_out);
 
 /*
  * nmf_restrict - Y = R X, the full-weighting restriction of Eq. (4.1) applied

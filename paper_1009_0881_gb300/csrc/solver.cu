@@ -103,6 +103,22 @@ struct ScheduleBuilder {
     }
 };
 
+// Algorithm V-cycle with explicit counts: c[0 .. L-2] before-sweeps of levels 0 .. L-2,
+// c[L-1] on the coarsest level, c[L .. 2L-2] after-sweeps of levels L-2 .. 0 (run order).
+std::vector<Op> build_schedule_counts(int L, const int64_t* c) {
+    ScheduleBuilder b;
+    for (int l = 0; l + 1 < L; ++l) {
+        b.sweeps(l, c[l]);
+        b.ops.push_back({OP_RESTRICT_V, l, 0});
+    }
+    b.sweeps(L - 1, c[L - 1]);
+    for (int l = L - 2; l >= 0; --l) {
+        b.ops.push_back({OP_PROLONG_V, l, 0});
+        b.sweeps(l, c[2 * L - 2 - l]);
+    }
+    return b.ops;
+}
+
 std::vector<Op> build_schedule(nmf_cycle cyc, int L, int64_t K) {
     ScheduleBuilder b;
     if (cyc == NMF_NESTED)
@@ -1236,6 +1252,13 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     const nmf_cycle cyc = opt ? opt->cycle : NMF_VCYCLE;
     if (cyc != NMF_VCYCLE && cyc != NMF_NESTED && cyc != NMF_FMG && cyc != NMF_WCYCLE)
         return fail(h, NMF_EINVAL, "unknown cycle");
+    const int64_t* counts = opt ? opt->level_sweeps : nullptr;
+    if (counts) {
+        if (cyc != NMF_VCYCLE || opt->coarsen_columns)
+            return fail(h, NMF_EINVAL, "explicit level sweeps are for the V-cycle without column coarsening");
+        for (int i = 0; i < 2 * L - 1; ++i)
+            if (counts[i] < 0) return fail(h, NMF_EINVAL, "negative sweep count");
+    }
     if (opt && opt->coarsen_columns) return solve_columns_impl(h, M, m, n, gh, gw, r, algo, L, K, opt, V, W);
     const int64_t stop_after = opt ? opt->stop_after : 0;
     const bool trace = opt && opt->trace && opt->trace_len > 0;
@@ -1256,13 +1279,16 @@ int solve_impl(nmf_ctx* h, const float* M, int64_t m, int64_t n, int gh, int gw,
     CK(cudaMemcpyAsync(h->h_bad, p.d_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
 
     // the whole hierarchy + schedule as one cached CUDA graph
-    char key[256];
-    snprintf(key, sizeof key, "solve:%lld:%lld:%d:%d:%d:%d:%d:%d:%d:%lld:%lld:%p", (long long)m, (long long)n, gh, gw,
+    char kbuf[256];
+    snprintf(kbuf, sizeof kbuf, "solve:%lld:%lld:%d:%d:%d:%d:%d:%d:%d:%lld:%lld:%p", (long long)m, (long long)n, gh, gw,
              r, (int)algo, L, K, (int)cyc, (long long)stop_after, (long long)(trace ? opt->trace_len : 0),
              (void*)h->ws);
-    const std::vector<Op> ops = build_schedule(cyc, L, K);
+    std::string key = kbuf;
+    if (counts)
+        for (int i = 0; i < 2 * L - 1; ++i) key += ":" + std::to_string((long long)counts[i]);
+    const std::vector<Op> ops = counts ? build_schedule_counts(L, counts) : build_schedule(cyc, L, K);
     GraphEntry ge;
-    rc = cached_graph(h, key, &ge, [&](int64_t* fine) {
+    rc = cached_graph(h, key.c_str(), &ge, [&](int64_t* fine) {
         cudaError_t e = enqueue_hierarchy(h, p);
         if (e == cudaSuccess) e = enqueue_schedule(h, p, ops, algo, stop_after, trace, fine);
         return e;
@@ -1912,6 +1938,22 @@ int64_t nmf_schedule(nmf_cycle cycle, int levels, int iters, int64_t* sweeps_per
             if (sweeps_per_level) sweeps_per_level[op.level] += op.count;
         }
     return total;
+}
+
+int nmf_time_schedule(int levels, double budget, const double* costs, int64_t* level_sweeps_out) {
+    if (levels < 1 || levels > 16 || !costs || !level_sweeps_out || !(budget >= 0.0)) return NMF_EINVAL;
+    for (int l = 0; l < levels; ++l)
+        if (!(costs[l] > 0.0)) return NMF_EINVAL;
+    // share of level l: budget / 4^l; a quarter before, half after; the coarsest spends all
+    double share = budget;
+    const int L = levels;
+    for (int l = 0; l + 1 < L; ++l) {
+        level_sweeps_out[l] = (int64_t)std::floor(share / (4.0 * costs[l]) + 1e-9);
+        level_sweeps_out[2 * L - 2 - l] = (int64_t)std::floor(share / (2.0 * costs[l]) + 1e-9);
+        share /= 4.0;
+    }
+    level_sweeps_out[L - 1] = (int64_t)std::floor(share / costs[L - 1] + 1e-9);
+    return NMF_OK;
 }
 
 int nmf_solve(nmf_handle h, const float* M, int64_t m, int64_t n, int grid_h, int grid_w, int r, nmf_algo algo,

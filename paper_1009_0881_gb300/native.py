@@ -36,6 +36,7 @@ SIGNATURES = [
     ("nmf_solve_ex", _I, [_P, _P, _I64, _I64, _I, _I, _I, _I, _I, _I, _P, _P, _P]),
     ("nmf_error", _I, [_P, _P, _P, _P, _I64, _I64, _I, ctypes.POINTER(ctypes.c_double)]),
     ("nmf_schedule", _I64, [_I, _I, _I, ctypes.POINTER(_I64)]),
+    ("nmf_time_schedule", _I, [_I, ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     ("nmf_restrict", _I, [_P, _P, _I, _I, _I64, _P]),
     ("nmf_prolong", _I, [_P, _P, _I, _I, _I64, _P]),
     ("nmf_products", _I, [_P, _P, _P, _P, _I64, _I64, _I, _P, _P, _P, _P]),
@@ -69,7 +70,16 @@ class Problem(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("cycle", _I), ("stop_after", _I64), ("trace", ctypes.POINTER(ctypes.c_double)),
-                ("trace_len", _I64), ("trace_count", ctypes.POINTER(_I64)), ("coarsen_columns", _I)]
+                ("trace_len", _I64), ("trace_count", ctypes.POINTER(_I64)), ("level_sweeps", ctypes.POINTER(_I64)),
+                ("coarsen_columns", _I)]
+
+
+def _flat_level_sweeps(level_sweeps, levels: int):
+    """(pre, coarse, post) -> the 2 levels - 1 counts in run order (nmf_options.level_sweeps)."""
+    pre, coarse, post = level_sweeps
+    if len(pre) != levels - 1 or len(post) != levels - 1:
+        raise ValueError("level_sweeps needs levels - 1 before- and after-counts")
+    return np.array(list(pre) + [coarse] + list(post)[::-1], dtype=np.int64)
 
 
 class NMFError(RuntimeError):
@@ -167,9 +177,12 @@ class Handle:
 
     # --- entry points -------------------------------------------------------
     def solve(self, M, grid_h: int, grid_w: int, V, W, algo="hals", levels: int = 1, iters: int = 100,
-              cycle="vcycle", stop_after: int = 0, trace_len: int = 0, coarsen_columns: bool = False):
+              cycle="vcycle", stop_after: int = 0, trace_len: int = 0, coarsen_columns: bool = False,
+              level_sweeps=None):
         """nmf_solve_ex: improves V (m x r) and W (r x n) in place; returns the objective trace if asked.
-        coarsen_columns: the columns of M are a smooth sequence, coarsened by the V-cycle too."""
+        coarsen_columns: the columns of M are a smooth sequence, coarsened by the V-cycle too.
+        level_sweeps: (pre, coarse, post) explicit V-cycle counts, pre[l] / post[l] the sweeps of
+        level l + 1 before / after the coarser cycle (as time_schedule returns them)."""
         _check_f32(M, V, W)
         m, n = M.shape
         r = V.shape[1]
@@ -177,6 +190,10 @@ class Handle:
         opt.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
         opt.stop_after = stop_after
         opt.coarsen_columns = 1 if coarsen_columns else 0
+        counts = None
+        if level_sweeps is not None:
+            counts = _flat_level_sweeps(level_sweeps, levels)
+            opt.level_sweeps = counts.ctypes.data_as(ctypes.POINTER(_I64))
         trace = None
         count = _I64(0)
         if trace_len > 0:
@@ -382,3 +399,20 @@ def schedule(cycle: str, levels: int, iters: int) -> list[int]:
     if total < 0:
         raise NMFError(int(total), "nmf_schedule failed")
     return list(out)
+
+
+def time_schedule(budget: float, costs) -> tuple[list[int], int, list[int]]:
+    """nmf_time_schedule: (pre, coarse, post) V-cycle counts for a time budget and per-level
+    sweep costs (host-only, no GPU needed)."""
+    lib = load()
+    L = len(costs)
+    if L < 1:
+        raise NMFError(NMF_EINVAL, "time_schedule needs at least one level")
+    c = (ctypes.c_double * L)(*[float(x) for x in costs])
+    out = (_I64 * (2 * L - 1))()
+    rc = lib.nmf_time_schedule(L, float(budget), c, out)
+    if rc != 0:
+        raise NMFError(int(rc), "nmf_time_schedule failed")
+    flat = list(out)
+    return flat[:L - 1], flat[L - 1], flat[L:][::-1]
+

@@ -407,3 +407,39 @@ def test_hbm_budget_enforced():
     with native.Handle(0, hbm_budget_bytes=1 << 16) as small:
         with pytest.raises(native.NMFError, match="ENOMEM"):
             small.solve(p.M, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=3, iters=4)
+
+
+# ------------------------------------------ V-cycles with explicit level counts
+
+@pytest.mark.parametrize("name", ["grid19_hals_timed_L3", "grid19_mu_timed_L3"])
+def test_time_split_vcycle_matches_oracle(h, name):
+    # the split of a 500-sweep budget with GB300's per-level sweep costs (tests/golden)
+    g = GOLDEN[name]
+    gh, gw, n, r, sigma = synth.WORKLOADS[g["workload"]]
+    p = synth.make_problem(gh, gw, n, r, sigma=sigma)
+    V, W = p.V.copy(), p.W.copy()
+    pre, coarse, post = g["level_sweeps"]
+    tr = h.solve(p.M, gh, gw, V, W, g["algo"], levels=3, level_sweeps=(pre, coarse, post), trace_len=2000)
+    assert len(tr) == pre[0] + post[0]
+    f = o.objective(p.M, V, W)
+    assert abs(f - g["objective"]) <= 1e-3 * g["objective"], (f, g["objective"])
+
+
+def test_table1_counts_are_the_vcycle(h):
+    p = _problem(("grid16_n1000_r10", None))
+    K = 40
+    V1, W1 = p.V.copy(), p.W.copy()
+    h.solve(p.M, 16, 16, V1, W1, "hals", levels=3, iters=K)
+    V2, W2 = p.V.copy(), p.W.copy()
+    h.solve(p.M, 16, 16, V2, W2, "hals", levels=3, level_sweeps=([K // 4] * 2, K, [K // 2] * 2))
+    np.testing.assert_array_equal(V1, V2)
+    np.testing.assert_array_equal(W1, W2)
+
+
+def test_level_sweeps_outside_the_vcycle_rejected(h):
+    p = _problem(("grid16_n1000_r10", None))
+    with pytest.raises(native.NMFError):
+        h.solve(p.M, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=2, cycle="fmg", level_sweeps=([1], 2, [1]))
+    with pytest.raises(native.NMFError):
+        h.solve(p.M, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=2, level_sweeps=([-1], 2, [1]))
+    h.solve(p.M, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=2, level_sweeps=([0], 2, [0]))
