@@ -471,7 +471,7 @@ def analysis(args, h, prob, Md, V0d, W0d, Vd, Wd, stream, sched, err, gh, gw, m,
         if not args.no_sequence_table:
             out["image_sequence"] = sequence_table(h, stream, golden)
         out["time_split_vcycle"] = {a: time_split_vcycle(args, h, Md, V0d, W0d, Vd, Wd, stream, golden, gh, gw, a)
-                                    for a in ("hals", "mu")}
+                                    for a in ("hals", "mu", "anls")}
     if not args.no_precision_form:
         out["precision_form"] = precision_form(args)
     if not args.no_batched_form:
