@@ -168,6 +168,11 @@ typedef struct {
     int status;         /* nmf_status of this problem */
     int64_t sweeps_run; /* sweeps executed over all levels */
     double objective;   /* ||M - VW||_F of the result, FP64 accumulation */
+    /* input */
+    const int64_t* level_sweeps; /* optional: explicit V-cycle counts as nmf_options.level_sweeps
+                                    (2 levels - 1 entries, caller-owned until the call returns or
+                                    the served request completes); NULL: the counts iters gives.
+                                    Not taken by nmf_solve_grouped (NMF_EINVAL). */
 } nmf_problem;
 
 /*

@@ -1517,8 +1517,18 @@ int check_problems(nmf_ctx* h, const nmf_problem* probs, int count) {
             return fail(h, NMF_EINVAL, "problem %d: unknown algorithm", i);
         if (q.cycle != NMF_VCYCLE && q.cycle != NMF_NESTED && q.cycle != NMF_FMG && q.cycle != NMF_WCYCLE)
             return fail(h, NMF_EINVAL, "problem %d: unknown cycle", i);
+        if (q.level_sweeps) {
+            if (q.cycle != NMF_VCYCLE) return fail(h, NMF_EINVAL, "problem %d: explicit counts need the V-cycle", i);
+            for (int k = 0; k < 2 * q.levels - 1; ++k)
+                if (q.level_sweeps[k] < 0) return fail(h, NMF_EINVAL, "problem %d: negative sweep count", i);
+        }
     }
     return NMF_OK;
+}
+
+// The operations a batched problem runs: its explicit counts, or its cycle's.
+std::vector<Op> problem_schedule(const nmf_problem& q) {
+    return q.level_sweeps ? build_schedule_counts(q.levels, q.level_sweeps) : build_schedule(q.cycle, q.levels, q.iters);
 }
 
 int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
@@ -1559,6 +1569,8 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
         snprintf(buf, sizeof buf, ":%lld,%lld,%d,%d,%d,%d,%d,%d,%d,%.3g", (long long)q.m, (long long)q.n, q.grid_h,
                  q.grid_w, q.r, (int)q.algo, q.levels, q.iters, (int)q.cycle, q.rel_tol);
         key += buf;
+        if (q.level_sweeps)
+            for (int k = 0; k < 2 * q.levels - 1; ++k) key += "/" + std::to_string((long long)q.level_sweeps[k]);
     }
     snprintf(buf, sizeof buf, ":%p", (void*)h->ws);
     key += buf;
@@ -1577,8 +1589,7 @@ int batch_impl(nmf_ctx* h, nmf_problem* probs, int count) {
             e = enqueue_hierarchy(h, p);
             int64_t fine = 0;
             if (e == cudaSuccess)
-                e = enqueue_schedule(h, p, build_schedule(q.cycle, q.levels, q.iters), q.algo, 0, false, &fine,
-                                     q.rel_tol);
+                e = enqueue_schedule(h, p, problem_schedule(q), q.algo, 0, false, &fine, q.rel_tol);
             if (e == cudaSuccess)
                 e = error_launch(p.lv[0].M, p.ldm, p.lv[0].V, p.Wt, p.rp, p.m, p.n, p.r, p.err_part,
                                  p.conv_state + 2, h->stream);
@@ -1631,7 +1642,7 @@ int batch_results(nmf_ctx* h, nmf_problem* probs, const std::vector<Plan>& plans
         CK(cudaMemcpy(&cnt, p.conv_count, sizeof cnt, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(&obj, p.conv_state + 2, sizeof obj, cudaMemcpyDeviceToHost));
         // sweeps: the whole schedule, minus the watched finest-level run replaced by its counted part
-        const std::vector<Op> ops = build_schedule(q.cycle, q.levels, q.iters);
+        const std::vector<Op> ops = problem_schedule(q);
         int last_fine = -1;
         int64_t total = 0;
         for (int k = 0; k < (int)ops.size(); ++k)
@@ -1681,6 +1692,7 @@ int grouped_impl(nmf_ctx* h, nmf_problem* probs, int count) {
             return fail(h, NMF_EINVAL, "problem %d: the grouped form runs HALS and MU only", i);
         if (q.levels != q0.levels || q.iters != q0.iters || q.cycle != q0.cycle)
             return fail(h, NMF_EINVAL, "problem %d: the grouped form needs one cycle, level count and budget", i);
+        if (q.level_sweeps) return fail(h, NMF_EINVAL, "problem %d: the grouped form takes no explicit counts", i);
     }
     CK(cudaSetDevice(h->device));
     h->launches = 0;

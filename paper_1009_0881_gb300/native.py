@@ -65,7 +65,8 @@ class Problem(ctypes.Structure):
     """nmf_problem of include/nmf.h."""
     _fields_ = [("M", _P), ("m", _I64), ("n", _I64), ("grid_h", _I), ("grid_w", _I), ("r", _I), ("algo", _I),
                 ("levels", _I), ("iters", _I), ("cycle", _I), ("rel_tol", ctypes.c_double), ("V", _P), ("W", _P),
-                ("status", _I), ("sweeps_run", _I64), ("objective", ctypes.c_double)]
+                ("status", _I), ("sweeps_run", _I64), ("objective", ctypes.c_double),
+                ("level_sweeps", ctypes.POINTER(_I64))]
 
 
 class Options(ctypes.Structure):
@@ -314,7 +315,8 @@ class Handle:
 
 
 def fill_problem(q: Problem, d: dict) -> Problem:
-    """Marshal a problem dict (M, grid_h, grid_w, V, W, algo, levels, iters, cycle, rel_tol) into q."""
+    """Marshal a problem dict (M, grid_h, grid_w, V, W, algo, levels, iters, cycle, rel_tol and
+    optionally level_sweeps = (pre, coarse, post)) into q."""
     _check_f32(d["M"], d["V"], d["W"])
     q.M = _ptr(d["M"])
     q.m, q.n = d["M"].shape
@@ -329,6 +331,10 @@ def fill_problem(q: Problem, d: dict) -> Problem:
     q.rel_tol = d.get("rel_tol", 0.0)
     q.V = _ptr(d["V"])
     q.W = _ptr(d["W"])
+    if d.get("level_sweeps") is not None:
+        # kept in the dict: the library reads it until the solve or the served request ends
+        d["_level_sweeps_flat"] = _flat_level_sweeps(d["level_sweeps"], q.levels)
+        q.level_sweeps = d["_level_sweeps_flat"].ctypes.data_as(ctypes.POINTER(_I64))
     return q
 
 

@@ -133,3 +133,26 @@ def test_batch_of_uneven_sizes_against_oracle(h):
     if key == "objective_bf16":
         assert float(np.median(errs)) <= BF16_SAMPLE_MEDIAN
     print(f"batch of 64 against the oracle: max rel. error {max(errs):.2e}, median {float(np.median(errs)):.2e}")
+
+
+def test_batch_with_explicit_counts_equals_alone(h):
+    # problems carrying explicit V-cycle counts (nmf_problem.level_sweeps) get the bits of a
+    # standalone solve with the same counts; a problem without them keeps its iters schedule
+    probs = _problems()[:4]
+    counts = [([2, 1], 5, [4, 3]), None, ([1, 0], 7, [2, 2]), ([3], 4, [5])]
+    batch = []
+    for (p, algo, L, K), ls in zip(probs, counts):
+        if ls is not None and len(ls[0]) != L - 1:
+            ls = ([1] * (L - 1), 3, [2] * (L - 1))
+        batch.append(dict(M=p.M, grid_h=p.grid_h, grid_w=p.grid_w, V=p.V.copy(), W=p.W.copy(), algo=algo,
+                          levels=L, iters=K, level_sweeps=ls))
+    res = h.solve_batch(batch)
+    for (p, algo, L, K), d, (st, sweeps, obj) in zip(probs, batch, res):
+        assert st == 0
+        ls = d["level_sweeps"]
+        if ls is not None:
+            assert sweeps == sum(ls[0]) + ls[1] + sum(ls[2])
+        V, W = p.V.copy(), p.W.copy()
+        h.solve(p.M, p.grid_h, p.grid_w, V, W, algo, levels=L, iters=K, level_sweeps=ls)
+        np.testing.assert_array_equal(d["V"], V)
+        np.testing.assert_array_equal(d["W"], W)
