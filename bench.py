@@ -492,7 +492,7 @@ TRAFFIC = {
     "half_sweep_kernel": {"bytes": 0.5 * (4.969728e6 + 4.232192e6), "src": "a16cd947a6743266",
                           "files": ("fused.cu", "fused.cuh", "rowupdate.cuh", "ptx.cuh", "nmf_internal.cuh"),
                           "scope": "mean of the finest-level V-step (64-row tiles) and W-step (32-row tiles) launches, 19x19 grid n=2429 r=49"},
-    "tc_gemm_kernel": {"bytes": 268.152832e6 + 12.926464e6, "src": "61770f2562ba1e3d",
+    "tc_gemm_kernel": {"bytes": 268.110080e6 + 12.589056e6, "src": "77970ec086c9a0b9",
                        "files": ("tc_gemm.cu", "tc_gemm.cuh", "ptx.cuh", "nmf_internal.cuh"),
                        "scope": "finest-level V-step product, 256x256 grid n=2000 r=64"},
 }
