@@ -184,3 +184,19 @@ def test_outside_its_scope_is_rejected(h):
     # the handle stays usable
     res = h.solve_batch([d for _, d in _group(SHAPES[:2], "hals", 2, 4)], grouped=True)
     assert all(st == 0 for st, _, _ in res)
+
+
+@pytest.mark.parametrize("cycle", ["ni", "fmg", "wcycle"])
+def test_other_cycles_against_oracle(h, cycle):
+    # every cycle the schedule builder knows runs grouped: the result within 1e-3 of the FP64
+    # oracle's objective for the same cycle (shapes whose coarsest grid keeps r pixels)
+    g = _group(WELL_POSED[:3], "hals", 3, 12)
+    for _, d in g:
+        d["cycle"] = cycle
+    res = h.solve_batch([d for _, d in g], grouped=True)
+    for (p, d), (st, sweeps, obj) in zip(g, res):
+        assert st == 0
+        Vo, Wo = o.solve(p.M, d["grid_h"], d["grid_w"], p.V, p.W, "hals", levels=3, K=12, cycle=cycle)
+        fo = o.objective(p.M, Vo, Wo)
+        assert abs(obj - fo) <= 1e-3 * fo, (cycle, p.M.shape, obj, fo)
+        assert sweeps == sum(native.schedule(cycle, 3, 12))
