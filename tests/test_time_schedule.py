@@ -33,3 +33,16 @@ def test_time_split_rejects_bad_costs(native):
     for costs in ([1.0, 0.0], [1.0, -2.0], []):
         with pytest.raises(native.NMFError):
             native.time_schedule(10.0, costs)
+
+
+def test_level_sweeps_run_order(native):
+    # (pre, coarse, post) with pre[l] / post[l] for level l + 1 -> the run order of
+    # nmf_options.level_sweeps: pre_1 .. pre_{L-1}, coarse, post_{L-1} .. post_1
+    flat = native._flat_level_sweeps(([11, 12, 13], 40, [21, 22, 23]), 4)
+    assert flat.tolist() == [11, 12, 13, 40, 23, 22, 21]
+    assert native._flat_level_sweeps(([], 7, []), 1).tolist() == [7]
+    with pytest.raises(ValueError):
+        native._flat_level_sweeps(([1], 2, [1, 2]), 2)
+    # the library's split comes back in the same (pre, coarse, post) form
+    pre, coarse, post = native.time_schedule(1000.0, [10.0, 8.0, 5.0])
+    assert native._flat_level_sweeps((pre, coarse, post), 3).tolist() == [25, 7, 12, 15, 50]
