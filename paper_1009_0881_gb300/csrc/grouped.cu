@@ -16,6 +16,9 @@
 
 namespace nmfk {
 
+static_assert(alignof(GroupDesc) >= 64 && sizeof(GroupDesc) % 64 == 0,
+              "tensor maps in an array of descriptors must stay 64-byte aligned");
+
 namespace {
 
 using rowupd::f4add;

@@ -22,9 +22,10 @@ namespace nmfk {
 
 constexpr int kGroupTile = 64;  // rows of the factor per tile
 
-// One (problem, level, half) of a grouped solve, in device memory.  The tensor maps
-// are the half-sweep's operands (X: K x Na columns, box 64 x 32; Y: K x rp, box br x 32).
-struct alignas(64) GroupDesc {
+// One (problem, level, half) of a grouped solve, in device memory (the tensor maps carry
+// their own alignment, which an array of descriptors keeps).  The tensor maps are the
+// half-sweep's operands (X: K x Na columns, box 64 x 32; Y: K x rp, box br x 32).
+struct GroupDesc {
     CUtensorMap tmX;
     CUtensorMap tmY;
     float* F;            // Na x rp factor, updated in place
