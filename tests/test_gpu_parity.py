@@ -443,3 +443,16 @@ def test_level_sweeps_outside_the_vcycle_rejected(h):
     with pytest.raises(native.NMFError):
         h.solve(p.M, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=2, level_sweeps=([-1], 2, [1]))
     h.solve(p.M, 16, 16, p.V.copy(), p.W.copy(), "hals", levels=2, level_sweeps=([0], 2, [0]))
+
+
+@pytest.mark.parametrize("L,counts", [(1, ([], 7, [])), (4, ([3, 2, 1], 5, [4, 3, 2]))])
+def test_explicit_counts_against_oracle(h, L, counts):
+    # one level (the counts are the plain algorithm's sweeps) and four levels with distinct
+    # counts on a ragged grid, element-wise against the oracle's explicit-count V-cycle
+    p = synth.make_problem(13, 11, 90, 3, data_seed=17)
+    V, W = p.V.copy(), p.W.copy()
+    h.solve(p.M, 13, 11, V, W, "hals", levels=L, level_sweeps=counts)
+    Vo, Wo = o.solve(p.M, 13, 11, p.V, p.W, "hals", levels=L, level_sweeps=counts)
+    assert rel(V, Vo) <= 1e-4 and rel(W, Wo) <= 1e-4, (rel(V, Vo), rel(W, Wo))
+    fo = o.objective(p.M, Vo, Wo)
+    assert abs(o.objective(p.M, V, W) - fo) <= 1e-5 * fo
