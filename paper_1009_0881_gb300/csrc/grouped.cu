@@ -28,6 +28,9 @@ constexpr int NST = 4;          // pipeline stages
 constexpr int NT = 256;         // threads
 constexpr int BA = kGroupTile;  // rows of F per tile
 
+static_assert(NST * KS * BA >= BA * kMaxRank && NST * KS * kMaxRank >= BA * kMaxRank,
+              "the ring must hold the product rows and F G of a tile");
+
 struct GSmem {
     size_t xs, ys, gs, ginv, ared, fn, dn, red, bar, slot, total;
 };
@@ -39,11 +42,13 @@ __host__ __device__ inline GSmem gsmem_layout() {
     size_t o = 0;
     s.xs = o;   o = galign(o + sizeof(float) * NST * KS * BA, 128);
     s.ys = o;   o = galign(o + sizeof(float) * NST * KS * kMaxRank, 128);
+    // the product rows and F G live in the ring's buffers once the product is done (no copy is
+    // in flight then: every stage of the tile has been waited for and read)
+    s.ared = s.xs;
+    s.dn = s.ys;
     s.gs = o;   o = galign(o + sizeof(float) * kMaxRank * kMaxRank, 128);
     s.ginv = o; o = galign(o + sizeof(float) * kMaxRank, 128);
-    s.ared = o; o = galign(o + sizeof(float) * BA * kMaxRank, 128);
     s.fn = o;   o = galign(o + sizeof(float) * BA * kMaxRank, 128);
-    s.dn = o;   o = galign(o + sizeof(float) * BA * kMaxRank, 128);
     s.red = o;  o = galign(o + sizeof(double) * (NT / 32), 128);
     s.bar = o;  o = galign(o + sizeof(uint64_t) * NST, 128);
     s.slot = o; o = galign(o + sizeof(int), 128);
@@ -235,7 +240,7 @@ __device__ __forceinline__ void group_tile(const GroupDesc* d, int tile, const B
     __syncthreads();  // shared buffers are free for the next tile
 }
 
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, 2)
     grouped_half_sweep_kernel(const GroupDesc* __restrict__ descs, const GroupItem* __restrict__ items, int nitems,
                               int* counter) {
     extern __shared__ __align__(128) unsigned char smem_raw[];

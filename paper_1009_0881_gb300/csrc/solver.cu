@@ -1855,7 +1855,7 @@ int grouped_impl(nmf_ctx* h, nmf_problem* probs, int count) {
                     e = grouped_gram_launch(d_jobs + (size_t)g * count, count, max_f4, h->stream);
                     if (e == cudaSuccess)
                         e = grouped_half_sweep_launch(d_desc, d_items + item_off[g], (int)(item_off[g + 1] - item_off[g]),
-                                                      d_counters + ph++, h->num_sms, h->stream);
+                                                      d_counters + ph++, 2 * h->num_sms, h->stream);
                 }
                 if (e == cudaSuccess && k == last_fine && nconv) e = grouped_converge_launch(d_conv, nconv, h->stream);
             }
