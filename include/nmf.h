@@ -192,7 +192,8 @@ int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count);
  * problems' factors from a work-list (the product with M over the whole of K, the HALS or
  * MU update of the tile's rows, the Gram slab of the new rows), after one launch that
  * reduces each problem's Gram slabs; the whole solve is one CUDA graph.  Problems that
- * meet their stopping rule drop out of the later launches.  Requirements (NMF_EINVAL
+ * meet their stopping rule do no further work (their tiles return as soon as they are taken).
+ * The launches take up to two CTAs per SM.  Requirements (NMF_EINVAL
  * otherwise): an NMF_FP32 handle, algorithms NMF_HALS or NMF_MU, and the same cycle,
  * levels and iters for every problem; sizes and ranks may differ.  A problem's result
  * does not depend on the rest of the group; it differs from nmf_solve's in the order of
