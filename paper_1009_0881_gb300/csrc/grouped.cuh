@@ -2,7 +2,7 @@
 // (V-step or W-step of the schedule's current sweep) of many independent problems.
 //
 // Each problem contributes its 64-row tiles of the factor being updated; the CTAs
-// of the launch (one per SM) take tiles from a shared work-list through an atomic
+// of the launch (two per SM) take tiles from a shared work-list through an atomic
 // counter, so small and large problems share the device in one launch.  A tile is
 // the whole product over K (no split across CTAs), the HALS or MU update of its rows
 // and the Gram slab of its new rows; the Gram matrix it updates with is reduced from
@@ -74,7 +74,7 @@ size_t grouped_smem_bytes();
 // The reduction of every job's slabs (one launch); `jobs` in device memory.
 cudaError_t grouped_gram_launch(const GramJob* jobs, int njobs, int max_f4, cudaStream_t st);
 // One persistent launch over `nitems` work items; `counter` (zero before the launch) hands
-// them out.  `ctas`: CTAs of the launch (one per SM).
+// them out.  `ctas`: CTAs of the launch (two per SM fit).
 cudaError_t grouped_half_sweep_launch(const GroupDesc* descs, const GroupItem* items, int nitems, int* counter,
                                       int ctas, cudaStream_t st);
 
