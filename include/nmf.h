@@ -193,8 +193,9 @@ int nmf_solve_batch(nmf_handle h, nmf_problem* probs, int count);
  * MU update of the tile's rows, the Gram slab of the new rows), after one launch that
  * reduces each problem's Gram slabs; the whole solve is one CUDA graph.  Problems that
  * meet their stopping rule do no further work (their tiles return as soon as they are taken).
- * Requirements (NMF_EINVAL otherwise): an NMF_FP32 or NMF_AUTO handle, algorithms NMF_HALS or NMF_MU, and the same cycle,
- * levels and iters for every problem; sizes and ranks may differ.  A problem's result
+ * Requirements (NMF_EINVAL otherwise): an NMF_FP32 or NMF_AUTO handle, algorithms NMF_HALS
+ * or NMF_MU, and the same cycle, levels and iters for every problem; sizes and ranks may
+ * differ.  A problem's result
  * does not depend on the rest of the group; it differs from nmf_solve's in the order of
  * the float32 sums (nmf_solve splits K across a thread-block cluster).  Outputs and
  * statuses as nmf_solve_batch.
